@@ -1,0 +1,132 @@
+/*
+ * lingam.h -- C ABI of the GB300 DirectLiNGAM causal-ordering library.
+ *
+ * Problem statement (ParaLiNGAM paper, Sec. II-B and II-C): the input is a
+ * data matrix X of p variables by n samples, row i holding the n samples of
+ * variable X_i; the model is X = B X + N with B strictly lower triangular in
+ * some causal order (Eq. base_mat).  The library returns a causal order K
+ * (Algorithm 1) and the weighted adjacency matrix B estimated from K by
+ * ordinary least squares of every variable on its predecessors.
+ *
+ * Each iteration (Algorithm 3) compares every still-unordered pair of
+ * normalised variables with the likelihood-ratio measure of Eq. Itest, using
+ * the entropy approximation of Eq. HApp and the closed-form normalised
+ * residual of Eq. var_update, adds min(0, I)^2 to the scores (Algorithm 2),
+ * takes the variable of lowest score as the root, and removes it from the
+ * data (Algorithm 7, UpdateData) and from the covariance matrix (Eq.
+ * CovUpdate, Algorithm 8).  A pair is evaluated once for both directions
+ * (messaging, Sec. III-A: I(j,i) = -I(i,j)) and a variable stops being
+ * compared once its partial score exceeds the best complete score (threshold,
+ * Sec. III-B); both shortcuts leave the result unchanged.
+ *
+ * Conventions for every entry point:
+ *   - Errors are returned as lingam_status codes; nothing is thrown across
+ *     the ABI.  Outputs are written only when the call returns LINGAM_OK.
+ *   - The caller owns every buffer, the workspace included.  The library
+ *     allocates no memory and keeps no state between calls.
+ *   - Data pointers may point to host or device memory; the library tells
+ *     them apart with cudaPointerGetAttributes.  Host buffers are copied
+ *     inside the call.  All device work runs on opts->stream and the call
+ *     returns after that stream has drained (it is synchronous).
+ *   - The device is the CUDA device current on the calling thread.
+ */
+#ifndef LINGAM_H
+#define LINGAM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LINGAM_OK = 0,
+    LINGAM_EINVAL = -1,       /* bad argument: p < 1, n < 3, NULL pointer, bad option, workspace too small */
+    LINGAM_EDEGENERATE = -2,  /* zero variance row or residual, |rho| >= 1, non-finite data */
+    LINGAM_ENOMEM = -3,       /* reserved: the library itself never allocates */
+    LINGAM_ECUDA = -4,        /* a CUDA runtime call or kernel launch failed */
+    LINGAM_ETIMEOUT = -5      /* a bounded device-side wait ran out (opts.timeout_s) */
+} lingam_status;
+
+/* opts.precision */
+enum { LINGAM_FP64 = 0, LINGAM_MIXED = 1 };
+/* opts.input_dtype */
+enum { LINGAM_F32 = 0, LINGAM_F64 = 1 };
+
+typedef struct {
+    int precision;           /* LINGAM_MIXED (FP32 pair measure, FP64 covariance and B) or LINGAM_FP64 */
+    int input_dtype;         /* element type of X: LINGAM_F32 or LINGAM_F64 */
+    int prune;               /* 1 = threshold pruning (Sec. III-B), 0 = compare every pair */
+    int reuse;               /* 1 = one evaluation per unordered pair (Sec. III-A), 0 = every ordered pair */
+    int tile_i, tile_j;      /* pair-tile shape override; 0 = autotuned */
+    int split_n;             /* sample-axis split override; 0 = autotuned */
+    double timeout_s;        /* bound on any device-side wait; <= 0 means 10 s */
+    void* stream;            /* cudaStream_t to run on; NULL = the legacy default stream */
+    const int* forced_order; /* NULL, or p variable indices (host memory): iteration k takes
+                                forced_order[k] as its root instead of the argmin; scores are still
+                                those of the current iteration.  Used for iteration-by-iteration checks. */
+} lingam_opts;
+
+typedef struct {
+    /* Each of these is NULL or a HOST array the library fills in. */
+    double* root_score;          /* [p] score S of the root chosen at iteration k */
+    double* margin_lb;           /* [p] lower bound of (second lowest score - root score) at iteration k;
+                                    +inf when a single variable is left */
+    long long* pairs_evaluated;  /* [p] pair evaluations at iteration k (unordered pairs when reuse = 1) */
+    double* scores;              /* [p*p] scores[k*p + v]: S_v at iteration k if v was compared with every
+                                    other remaining variable at that iteration; NaN if v was already
+                                    ordered or was pruned before completing */
+    /* Filled in whenever the report pointer is non-NULL (device time, CUDA events). */
+    double t_standardize_ms, t_gram_ms, t_order_ms, t_B_ms;
+    long long pairs_total;       /* sum of pairs_evaluated over the run */
+    long long pairs_unpruned;    /* sum over iterations of r(r-1)/2 (r(r-1) when reuse = 0) */
+} lingam_report;
+
+/* Fills *opts with the defaults: MIXED, F32, prune = reuse = 1, autotuned
+ * tiles, timeout 10 s, default stream, no forced order. */
+void lingam_default_opts(lingam_opts* opts);
+
+/* Size in bytes of the device workspace lingam_fit needs for a p x n problem
+ * with these options (NULL = defaults).  Returns 0 for invalid sizes.  The
+ * workspace must be device memory aligned to 256 bytes. */
+size_t lingam_workspace_size(long long p, long long n, const lingam_opts* opts);
+
+/*
+ * lingam_fit -- DirectLiNGAM (Algorithm 1) accelerated as in Algorithm 3.
+ *   X          p x n row-major samples, element type opts->input_dtype; host or device.
+ *   p, n       p >= 1 variables, n >= 3 samples.
+ *   order      [p] ints, host or device: order[k] = 0-based index of the k-th variable of the
+ *              causal order; order[0] is the first root (most exogenous variable).
+ *   B          [p*p] doubles, host or device, or NULL: B[i*p + j] = b_ij, the direct effect of X_j
+ *              on X_i in the units of X (Eq. base_linear); strictly lower triangular once rows
+ *              and columns are permuted into `order`.
+ *   workspace  device memory of at least lingam_workspace_size(p, n, opts) bytes.
+ *   opts       NULL = defaults.
+ *   report     NULL or a report to fill in.
+ * Returns LINGAM_OK or an error status.
+ */
+int lingam_fit(const void* X, long long p, long long n, int* order, double* B, void* workspace,
+               const lingam_opts* opts, lingam_report* report);
+
+/* Workspace for lingam_fit_batch over `count` datasets of sizes p[k] x n[k]. */
+size_t lingam_workspace_size_batch(int count, const long long* p, const long long* n, const lingam_opts* opts);
+
+/*
+ * lingam_fit_batch -- `count` independent problems (for instance bootstrap
+ * resamples).  X[k], order[k], B[k] as in lingam_fit for dataset k; B[k] may
+ * be NULL.  status[k] (host array, may be NULL) receives each dataset's
+ * status; report may be NULL or an array of `count` reports.  Returns the
+ * first non-OK dataset status, else LINGAM_OK.
+ */
+int lingam_fit_batch(int count, const void* const* X, const long long* p, const long long* n, int* const* order,
+                     double* const* B, void* workspace, const lingam_opts* opts, int* status,
+                     lingam_report* report);
+
+/* Static, human-readable name of a status code. */
+const char* lingam_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LINGAM_H */
