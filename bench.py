@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Benchmark of the DirectLiNGAM causal-ordering hot path on GB300.
+
+Workload: seeded synthetic LiNGAM data, p = 1000 variables, n = 10^4 samples,
+expected in-degree 2, FP32 storage (40 MB); mixed-precision path with
+threshold pruning and pair reuse.  One step = one full lingam_fit call
+(normalise, covariance, all p iterations of ordering, B fit) on inputs already
+resident in HBM.  Metric: pair-sample evaluations per second, counted as the
+unpruned-equivalent work sum_r r(r-1)/2 * n of one ordering (higher is better).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank fits its own dataset (seed = rank + 1): independent
+problems, weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+P_DEFAULT, N_DEFAULT = 1000, 10000
+L2_FLUSH_BYTES = 256 << 20
+# Pair kernel SFU roofline: per pair-sample 4 ex2 (32 per SM per clock on sm_103a)
+# plus 2 lg2 per 32 samples (16 per SM per clock).
+SFU_CLK_PER_PAIR_SAMPLE = 4.0 / 32.0 + (2.0 / 32.0) / 16.0
+
+
+def unpruned_pair_samples(p: int, n: int) -> float:
+    return float(sum(r * (r - 1) // 2 for r in range(2, p + 1))) * n
+
+
+def measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ clocks during the timed region
+class ClockSampler:
+    FIELDS = ("pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.bus_id and self.bus_id[-12:] not in parts[0].lower():
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5], parts[6], parts[7], parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        top = max(r[0] for r in rows)
+        loaded = [r for r in rows if r[0] >= 0.5 * top] or rows
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in loaded for k in range(4) if r[2 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_rate(X64: np.ndarray, target_s: float, seed: int = 7):
+    """Oracle FindRoot (Algorithm 2) over a subset of m variables, m sized so the
+    call takes about target_s seconds on all host cores.  Returns
+    (pair-samples/s, seconds, m, threads) in unpruned-equivalent units."""
+    import oracle
+    n = X64.shape[1]
+    rng = np.random.default_rng(seed)
+    m0 = 24
+    U0 = np.sort(rng.choice(X64.shape[0], m0, replace=False))
+    t = time.perf_counter()
+    oracle.find_root_scores(X64, U0)
+    t0 = max(time.perf_counter() - t, 1e-3)
+    m = int(min(X64.shape[0], max(m0, np.sqrt(target_s / t0 * m0 * (m0 - 1)))))
+    U = np.sort(rng.choice(X64.shape[0], m, replace=False))
+    t = time.perf_counter()
+    oracle.find_root_scores(X64, U)
+    dt = time.perf_counter() - t
+    return m * (m - 1) / 2 * n / dt, dt, m, oracle.num_threads(0)
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    from paper_2109_13993_gb300 import synth
+    d = synth.workload("p1000_n10000", seed=1)
+    X64 = d.X.astype(np.float32).astype(np.float64)
+    per_step_target = 8.0
+    for _ in range(args.warmup):
+        oracle_rate(X64, per_step_target)
+    rates, times, ms = [], [], []
+    for _ in range(args.steps):
+        r, dt, m, cores = oracle_rate(X64, per_step_target)
+        rates.append(r)
+        times.append(dt)
+        ms.append(m)
+    value = float(np.mean(rates))
+    sample = (f"oracle FindRoot (Algorithm 2, every ordered pair) over {int(np.mean(ms))} of the 1000 variables "
+              f"of the p=1000, n=10000 dataset per step; rate in unpruned-equivalent pair-samples")
+    line = {"impl": "reference", "metric": "pair-sample evals/s (unpruned-equivalent) at p=1000, n=1e4",
+            "value": value, "unit": "pair-samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "p1000_n10000 LiNGAM, expected in-degree 2, seed 1", "p": 1000, "n": 10000},
+            "cpu_baseline": {"value": value, "unit": "pair-samples/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "pair-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+def run_ours(args, rank: int, world: int):
+    import torch
+    import __graft_entry__ as entry
+    from paper_2109_13993_gb300 import lingam, synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    entry.build()
+    p, n = args.p, args.n
+    d = synth.workload("p1000_n10000", seed=1 + rank) if (p, n) == (P_DEFAULT, N_DEFAULT) else \
+        synth.lingam_dataset(p, n, 4.0 / max(p - 1, 1), seed=1 + rank)
+    X = torch.tensor(d.X.astype(np.float32), device=dev)
+    ws = lingam.alloc_workspace(lingam.workspace_size(p, n), device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def step(inp, out=None):
+        return lingam.fit(inp, precision="mixed", workspace=ws, timing=True, out=out)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(X)
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+    bus_id = f"{bus:02x}:00" if isinstance(bus, int) else None
+    step_ms, pair_ms, pairs, launches = [], [], [], []
+    with ClockSampler(bus_id) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = step(X)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            step_ms.append(e0.elapsed_time(e1))
+            pair_ms.append(res.times_ms["pair"])
+            pairs.append(res.pairs_total)
+            launches.append(res.kernel_launches)
+    clocks = clk.summary()
+    barrier()
+    tot_ms = float(np.sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    work = unpruned_pair_samples(p, n)
+    value = world * work / (ms_per_step / 1000.0)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    Xh = torch.tensor(d.X.astype(np.float32)).pin_memory()
+    order_h = torch.empty(p, dtype=torch.int32).pin_memory()
+    B_h = torch.empty((p, p), dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lingam.fit(Xh, precision="mixed", workspace=ws, out=(order_h, B_h))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_tot = float(np.sum(e2e_ms))
+    if dist is not None:
+        t = torch.tensor([e2e_tot], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+    e2e_value = world * work / (e2e_tot / args.steps / 1000.0)
+
+    # pair-kernel roofline (SFU bound), from the timed steps
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = props.multi_processor_count
+    peak = nsm * (1.0 / SFU_CLK_PER_PAIR_SAMPLE) * sm_max * 1e6
+    achieved = float(np.sum(pairs)) * n / (float(np.sum(pair_ms)) / 1000.0)
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-samples/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_pair_wave<float>",
+                "peak_basis": f"SFU: 4 ex2 + 1/16 lg2 per pair-sample, {nsm} SMs x 32 ex2/clk at sm_max {sm_max:.0f} MHz"}
+
+    line = {"metric": "pair-sample evals/s (unpruned-equivalent) at p=1000, n=1e4, mixed path",
+            "value": value, "unit": "pair-samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"p{p}_n{n} LiNGAM, expected in-degree 2, FP32 storage, seed = rank+1",
+                       "p": p, "n": n, "precision": "mixed", "prune": True, "reuse": True,
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"independent datasets x{world}"},
+            "ordering_ms": ms_per_step, "pairs_evaluated_per_step": int(np.mean(pairs)),
+            "pairs_unpruned_per_step": int(work // n), "pruned_fraction": 1.0 - float(np.mean(pairs)) / (work / n),
+            "gpu_launches": int(np.sum(launches)), "clocks": clocks, "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": "pair-samples/s", "h2d_bytes_per_step": int(p * n * 4),
+                    "d2h_bytes_per_step": int(p * 4 + p * p * 8)}}
+
+    if world == 1 and not args.no_fp64:
+        # FP64 GPU path vs mixed path on the same first iterations (same unpruned work)
+        k = args.fp64_iters
+        Xd = torch.tensor(d.X, device=dev)
+        ws64 = lingam.alloc_workspace(lingam.workspace_size(p, n, precision="fp64", input_dtype=np.float64), device=dev)
+        lingam.fit(X, precision="mixed", workspace=ws, max_iters=2)
+        rm = lingam.fit(X, precision="mixed", workspace=ws, max_iters=k)
+        r64 = lingam.fit(Xd, precision="fp64", workspace=ws64, max_iters=k)
+        w_k = float(sum(r * (r - 1) // 2 for r in range(p - k + 1, p + 1))) * n
+        line["fp64_path"] = {"iterations": k, "mixed_order_ms": rm.times_ms["order"],
+                             "fp64_order_ms": r64.times_ms["order"],
+                             "mixed_pair_samples_per_s": w_k / (rm.times_ms["order"] / 1000.0),
+                             "fp64_pair_samples_per_s": w_k / (r64.times_ms["order"] / 1000.0),
+                             "mixed_speedup": r64.times_ms["order"] / rm.times_ms["order"],
+                             "same_roots": bool(np.array_equal(rm.order[:k], r64.order[:k]))}
+        del ws64
+
+    if world == 1 and rank == 0 and not args.no_cpu:
+        X64 = d.X.astype(np.float32).astype(np.float64)
+        rate, dt, m, cores = oracle_rate(X64, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "pair-samples/s", "cores": cores, "kind": "oracle",
+                                "sample": f"oracle FindRoot (Algorithm 2, every ordered pair) over {m} of the "
+                                          f"{p} variables of the same dataset, {dt:.1f} s"}
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--p", type=int, default=P_DEFAULT)
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--fp64-iters", type=int, default=5)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -65,6 +65,10 @@ typedef struct {
     const int* forced_order; /* NULL, or p variable indices (host memory): iteration k takes
                                 forced_order[k] as its root instead of the argmin; scores are still
                                 those of the current iteration.  Used for iteration-by-iteration checks. */
+    int max_iters;           /* 0 = all p iterations; else stop after this many (order[k] = -1 beyond,
+                                B is then not computed).  Used to time a bounded prefix of a run. */
+    int timing;              /* 1 = also time the pair-comparison phase of every iteration (report
+                                t_pair_ms); adds two CUDA events per iteration */
 } lingam_opts;
 
 typedef struct {
@@ -80,10 +84,13 @@ typedef struct {
     double t_standardize_ms, t_gram_ms, t_order_ms, t_B_ms;
     long long pairs_total;       /* sum of pairs_evaluated over the run */
     long long pairs_unpruned;    /* sum over iterations of r(r-1)/2 (r(r-1) when reuse = 0) */
+    double t_pair_ms;            /* device time of the pair-comparison launches (opts.timing = 1), else 0 */
+    long long kernel_launches;   /* kernels this call launched */
 } lingam_report;
 
 /* Fills *opts with the defaults: MIXED, F32, prune = reuse = 1, autotuned
- * tiles, timeout 10 s, default stream, no forced order. */
+ * tiles, timeout 10 s, default stream, no forced order, all iterations, no
+ * per-iteration timing. */
 void lingam_default_opts(lingam_opts* opts);
 
 /* Size in bytes of the device workspace lingam_fit needs for a p x n problem

@@ -400,3 +400,113 @@ int oracle_pair_measures(const double* X, long n, const int* pi, const int* pj, 
 }
 
 int oracle_num_threads(int nthreads) { return resolve_threads(nthreads); }
+
+/* ---------------- scores of selected variables after a given prefix of roots ---------------- */
+
+typedef struct {
+    const double* Z; const double* H; const int* U; int r; long n; const int* vars; int m; double* S;
+    int next; int status; pthread_mutex_t mu;
+} varscore_job;
+
+static void* varscore_worker(void* arg) {
+    varscore_job* job = (varscore_job*)arg;
+    long n = job->n;
+    double* work = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+    if (!work) {
+        pthread_mutex_lock(&job->mu); job->status = ORACLE_ENOMEM; pthread_mutex_unlock(&job->mu);
+        return NULL;
+    }
+    /* work items: (variable k, partner position b); each item adds one term,
+       summed per variable afterwards in partner order */
+    for (;;) {
+        pthread_mutex_lock(&job->mu);
+        int item = job->next++;
+        int bad = job->status != ORACLE_OK;
+        pthread_mutex_unlock(&job->mu);
+        if (item >= job->m * job->r || bad) break;
+        int k = item / job->r, b = item % job->r;
+        int i = job->vars[k], j = job->U[b];
+        double term = 0.0;
+        if (i != j) {
+            double I;
+            int st = compare_normalised(job->Z + (size_t)i * n, job->Z + (size_t)j * n, job->H[i], job->H[j], n,
+                                        work, &I);
+            if (st != ORACLE_OK) {
+                pthread_mutex_lock(&job->mu); job->status = st; pthread_mutex_unlock(&job->mu);
+                break;
+            }
+            double mneg = I < 0.0 ? I : 0.0;
+            term = mneg * mneg;
+        }
+        job->S[item] = term;
+    }
+    free(work);
+    return NULL;
+}
+
+/*
+ * oracle_variable_scores: replay the roots prefix[0..k-1] on X (RegressRoot
+ * after each, Alg. 1), then return S_v (Alg. 2) for each v in vars[0..m-1]
+ * against the remaining set U.  out[m].  Every v must still be in U.
+ */
+int oracle_variable_scores(const double* X, int p, long n, const int* prefix, int k, const int* vars, int m,
+                           int nthreads, double* out) {
+    if (p < 1 || n < 3 || k < 0 || k >= p || m < 0) return ORACLE_EINVAL;
+    double* W = (double*)malloc(sizeof(double) * (size_t)p * (size_t)n);
+    int* U = (int*)malloc(sizeof(int) * (size_t)p);
+    char* in = (char*)calloc((size_t)p, 1);
+    double* tmp = (double*)malloc(sizeof(double) * (size_t)n);
+    double* Z = (double*)malloc(sizeof(double) * (size_t)p * (size_t)n);
+    double* H = (double*)malloc(sizeof(double) * (size_t)p);
+    double* terms = (double*)malloc(sizeof(double) * ((size_t)m * p + 1));
+    int st = ORACLE_OK;
+    if (!W || !U || !in || !tmp || !Z || !H || !terms) st = ORACLE_ENOMEM;
+    if (st == ORACLE_OK) {
+        memcpy(W, X, sizeof(double) * (size_t)p * (size_t)n);
+        for (int v = 0; v < p; ++v) in[v] = 1;
+        for (int it = 0; it < k && st == ORACLE_OK; ++it) {
+            int root = prefix[it];
+            if (root < 0 || root >= p || !in[root]) { st = ORACLE_EINVAL; break; }
+            in[root] = 0;
+            for (int w = 0; w < p && st == ORACLE_OK; ++w) {
+                if (!in[w]) continue;
+                st = oracle_regress(W + (size_t)w * n, W + (size_t)root * n, n, tmp);
+                if (st == ORACLE_OK) memcpy(W + (size_t)w * n, tmp, sizeof(double) * (size_t)n);
+            }
+        }
+    }
+    int r = 0;
+    if (st == ORACLE_OK) {
+        for (int v = 0; v < p; ++v) if (in[v]) U[r++] = v;
+        for (int a = 0; a < m; ++a) if (vars[a] < 0 || vars[a] >= p || !in[vars[a]]) st = ORACLE_EINVAL;
+    }
+    for (int a = 0; a < r && st == ORACLE_OK; ++a) {
+        int v = U[a];
+        st = oracle_standardize(W + (size_t)v * n, n, Z + (size_t)v * n);
+        if (st == ORACLE_OK) H[v] = oracle_entropy(Z + (size_t)v * n, n);
+    }
+    if (st == ORACLE_OK && m > 0) {
+        varscore_job job;
+        job.Z = Z; job.H = H; job.U = U; job.r = r; job.n = n; job.vars = vars; job.m = m; job.S = terms;
+        job.next = 0; job.status = ORACLE_OK;
+        pthread_mutex_init(&job.mu, NULL);
+        int nt = resolve_threads(nthreads);
+        pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nt);
+        int started = 0;
+        for (int t = 0; t < nt; ++t)
+            if (pthread_create(&th[t], NULL, varscore_worker, &job) == 0) ++started;
+        if (started == 0) varscore_worker(&job);
+        for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+        free(th);
+        pthread_mutex_destroy(&job.mu);
+        st = job.status;
+        if (st == ORACLE_OK)
+            for (int a = 0; a < m; ++a) {
+                double s = 0.0;
+                for (int b = 0; b < r; ++b) s += terms[(size_t)a * r + b];
+                out[a] = s;
+            }
+    }
+    free(W); free(U); free(in); free(tmp); free(Z); free(H); free(terms);
+    return st;
+}

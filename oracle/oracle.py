@@ -76,6 +76,8 @@ def _declare(L):
     L.oracle_fit.argtypes = [dp, ctypes.c_int, ctypes.c_long, ip, dp, dp, ip, ctypes.c_int]
     L.oracle_pair_measures.argtypes = [dp, ctypes.c_long, ip, ip, ctypes.c_int, ctypes.c_int, dp]
     L.oracle_num_threads.argtypes = [ctypes.c_int]
+    L.oracle_variable_scores.argtypes = [dp, ctypes.c_int, ctypes.c_long, ip, ctypes.c_int, ip, ctypes.c_int,
+                                         ctypes.c_int, dp]
 
 
 def _d(a: np.ndarray):
@@ -184,11 +186,24 @@ def fit(X, forced_order=None, want_scores: bool = True, want_B: bool = True, nth
     return order, B, S
 
 
+def variable_scores(X, prefix, vars_, nthreads: int = 0, lib=None) -> np.ndarray:
+    """S_v (Alg. 2) for each v in vars_, after the roots in prefix were removed (Alg. 1)."""
+    X = _rows(X)
+    pre = np.ascontiguousarray(prefix, dtype=np.int32)
+    vs = np.ascontiguousarray(vars_, dtype=np.int32)
+    out = np.zeros(len(vs))
+    st = (lib or _get()).oracle_variable_scores(_d(X), X.shape[0], X.shape[1], _i(pre) if len(pre) else None,
+                                                len(pre), _i(vs), len(vs), nthreads, _d(out))
+    if st != OK:
+        raise OracleError(st, "variable_scores")
+    return out
+
+
 class View:
     """The module's functions bound to one loaded oracle library (e.g. a test build)."""
 
     _names = ("constants", "num_threads", "standardize", "entropy", "regress", "pair_measure", "pair_measures",
-              "find_root_scores", "fit_B", "fit")
+              "find_root_scores", "fit_B", "fit", "variable_scores")
 
     def __init__(self, lib):
         import functools

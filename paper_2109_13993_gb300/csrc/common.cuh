@@ -1,0 +1,179 @@
+// common.cuh -- device-side types and helpers shared by the CUDA kernels of
+// the DirectLiNGAM ordering library (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lingam.h"
+
+namespace lingam {
+
+// ---------------------------------------------------------------------------
+// Constants of the entropy approximation, Eq. HApp (values as printed):
+//   H(u) = H(nu) - k1 [E log cosh u - beta]^2 - k2 [E u exp(-u^2/2)]^2.
+// H(nu) cancels in Eq. Itest, so the kernels carry H(u) - H(nu) only.
+constexpr double kK1 = 79.047;
+constexpr double kK2 = 7.4129;
+constexpr double kBeta = 0.37457;
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr double kLog2e = 1.44269504088896340736;
+
+// Pair-tile geometry of the FP32 pair kernel: a CTA owns TI rows x TJ columns
+// of the pair matrix; each thread owns 2 rows x 2 columns.
+constexpr int kTI = 32;
+constexpr int kTJ = 32;
+constexpr int kPairThreads = 256;
+constexpr int kChunk = 128;            // samples per shared-memory stage (FP32 path)
+constexpr int kChunk64 = 64;           // samples per stage (FP64 path)
+constexpr int kSub = 32;               // samples per product group (one lg2 per group)
+constexpr int kStages = 3;             // TMA ring depth
+constexpr int kSampleAlign = 128;      // n is padded with zero samples to a multiple of this
+constexpr int kMaxSplit = 64;
+
+// Flags per variable (ctl->flags[v]).
+constexpr int kAlive = 1;      // still in U
+constexpr int kColumned = 2;   // was a column of a wave this iteration => complete
+constexpr int kDead = 4;       // partial score exceeded the best complete score
+constexpr int kPick = 8;       // chosen as a column of the next wave (transient)
+
+// ---------------------------------------------------------------------------
+// Per-fit control block in device memory.  Written by kernels, read by the
+// host only after the final stream synchronisation.
+struct Ctl {
+    int status;          // first error (lingam_status), 0 = OK
+    int it;              // current iteration
+    int r;               // variables left in U at this iteration
+    int root;            // root chosen at this iteration
+    int done;            // iteration finished (root chosen)
+    int wave;            // wave counter within the iteration
+    int ncol;            // columns of the current wave
+    int nrow;            // rows of the current wave (columns first, then the rest)
+    int wave_ctas_done;  // CTAs of the current wave that have finished
+    int ntiles;          // row tiles of the current wave
+    int nsplit;          // sample splits of the current wave
+    int ncolumned;       // variables that have been a column this iteration
+    double best;         // lowest complete score so far this iteration
+    int best_var;        // variable holding `best`
+    int pad0;
+    long long pairs_it;  // pairs evaluated this iteration
+    unsigned long long timeout_ns;  // bound on device-side waits
+};
+
+// Device pointers of one fit, carved out of the caller's workspace.
+struct Fit {
+    int p;               // variables
+    int n;               // samples
+    int ld;              // padded row length (multiple of kSampleAlign)
+    int precision;       // LINGAM_MIXED or LINGAM_FP64
+    int prune;           // threshold pruning on
+    int reuse;           // pair reuse on
+    int has_forced;      // forced order given
+    int want_scores;     // fill the per-iteration score matrix
+    void* xt;            // p x ld normalised data (float or double)
+    double* mu;          // [p] row means
+    double* sd;          // [p] row standard deviations (divisor n-1)
+    double* sig;         // [p x p] covariance of the normalised rows, downdated each iteration
+    double* sig0;        // [p x p] covariance of the normalised rows before any removal
+    double* hx;          // [p] H(x_v) - H(nu) of the current normalised rows
+    double* part;        // [p] partial / full scores of the current iteration
+    double* prev;        // [p] scores of the previous iteration (ordering of candidates)
+    int* flags;          // [p]
+    int* sigma;          // [p] alive variables in candidate order
+    int* rows;           // [p] rows of the current wave (variable ids)
+    int* cols;           // [kTJ] columns of the current wave
+    int* order;          // [p] causal order (device copy)
+    const int* forced;   // [p] forced order or nullptr
+    int* scratch;        // [p] row list of the next wave (staging)
+    double* rowsum;      // [p] per row slot of the wave: sum over its columns of min(0, I)^2
+    double* colsum;      // [maxtiles x kTJ] per tile and column: sum over the tile's rows of max(0, I)^2
+    void* partials;      // [maxtiles x maxsplit x kPairThreads x 16] split partial moments (float or double)
+    double* inv_root;    // [p] 1/sqrt(1 - Sigma[w,root]^2) of the current removal
+    int* tile_cnt;       // [maxtiles] split arrival counters
+    double* rep_root_score;  // [p]
+    double* rep_margin;      // [p]
+    long long* rep_pairs;    // [p]
+    double* rep_scores;      // [p x p] or nullptr
+    // B fit
+    double* cmat;        // [p x p] covariance in causal order (original units)
+    double* rmat;        // [p x p] Cholesky factor (lower)
+    double* rinv;        // [p x p] inverse of the Cholesky factor
+    double* bout;        // [p x p] B (original indices)
+    Ctl* ctl;
+    int maxtiles;        // row tiles of a wave at most (ceil(p / kTI))
+    int maxsplit;        // sample splits at most
+};
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(Ctl* ctl, int code) { atomicCAS(&ctl->status, 0, code); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// MUFU base-2 exponential and logarithm (flush-to-zero approximations).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum (fixed shuffle tree, then fixed order over warps).
+// `red` must hold blockDim.x/32 elements.  All threads get the result.
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    T s = T(0);
+    for (int w = 0; w < nw; ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+
+// Block-wide exclusive scan of a 0/1 flag.  `red` holds blockDim.x/32 ints.
+// Returns the exclusive prefix of this thread; *total gets the block total.
+__device__ __forceinline__ int block_scan01(int flag, int* red, int* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    const int pre = __popc(m & ((1u << lane) - 1u));
+    __syncthreads();
+    if (lane == 0) red[wid] = __popc(m);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < nw; ++w) {
+        off += (w < wid) ? red[w] : 0;
+        tot += red[w];
+    }
+    *total = tot;
+    return off + pre;
+}
+
+// Entropy term of Eq. HApp minus H(nu), from the centred sums
+//   lcc = sum_t (log cosh u_t - beta),  g = sum_t u_t exp(-u_t^2/2),  over n samples.
+__host__ __device__ __forceinline__ double hterm(double lcc, double g, double n) {
+    const double a = lcc / n, b = g / n;
+    return -kK1 * a * a - kK2 * b * b;
+}
+__host__ __device__ __forceinline__ float hterm_f(float lcc, float g, float inv_n) {
+    const float a = lcc * inv_n, b = g * inv_n;
+    return -float(kK1) * a * a - float(kK2) * b * b;
+}
+
+}  // namespace lingam

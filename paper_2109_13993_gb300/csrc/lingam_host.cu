@@ -1,0 +1,391 @@
+// lingam_host.cu -- the C ABI of include/lingam.h: argument checks, workspace
+// layout, the launch sequence of Algorithm 3 on one stream, and the copies of
+// the results.  The library allocates no memory: every buffer is carved out
+// of the caller's workspace.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+#include "launch.h"
+#include "lingam.h"
+
+namespace lingam {
+
+cudaError_t ensure_smem_attr(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(func, dev);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess) done[key] = bytes;
+    return e;
+}
+
+constexpr long long kMaxP = 16384;
+constexpr size_t kAlign = 256;
+
+static size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t total = 0;
+    size_t off_xin, off_xt, off_mu, off_sd, off_sig, off_sig0, off_hx, off_part, off_prev, off_flags, off_sigma,
+        off_rows, off_cols, off_order, off_forced, off_scratch, off_rowsum, off_colsum, off_partials, off_invroot,
+        off_tilecnt, off_rs, off_rm, off_rp, off_rsc, off_cmat, off_rmat, off_rinv, off_bout, off_ctl;
+    int ld, maxtiles, maxsplit, esz;
+};
+
+static int chunk_of(int precision) { return precision == LINGAM_MIXED ? kChunk : kChunk64; }
+
+static Layout make_layout(long long p, long long n, int precision, int input_dtype) {
+    Layout L;
+    L.ld = int((n + kSampleAlign - 1) / kSampleAlign * kSampleAlign);
+    L.esz = precision == LINGAM_MIXED ? 4 : 8;
+    L.maxtiles = int((p + kTI - 1) / kTI);
+    L.maxsplit = std::max(1, std::min(kMaxSplit, L.ld / chunk_of(precision)));
+    const size_t in_esz = input_dtype == LINGAM_F32 ? 4 : 8;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    const size_t P = size_t(p), PP = size_t(p) * size_t(p);
+    L.off_ctl = take(sizeof(Ctl));
+    L.off_xin = take(P * size_t(n) * in_esz);
+    L.off_xt = take(P * size_t(L.ld) * L.esz);
+    L.off_mu = take(P * 8);
+    L.off_sd = take(P * 8);
+    L.off_sig = take(PP * 8);
+    L.off_sig0 = take(PP * 8);
+    L.off_hx = take(P * 8);
+    L.off_part = take(P * 8);
+    L.off_prev = take(P * 8);
+    L.off_flags = take(P * 4);
+    L.off_sigma = take(P * 4);
+    L.off_rows = take(P * 4);
+    L.off_cols = take(kTJ * 4);
+    L.off_order = take(P * 4);
+    L.off_forced = take(P * 4);
+    L.off_scratch = take(P * 4);
+    L.off_rowsum = take(P * 8);
+    L.off_colsum = take(size_t(L.maxtiles) * kTJ * 8);
+    L.off_partials = take(size_t(L.maxtiles) * L.maxsplit * kPairThreads * 16 * L.esz);
+    L.off_invroot = take(P * 8);
+    L.off_tilecnt = take(size_t(L.maxtiles) * 4);
+    L.off_rs = take(P * 8);
+    L.off_rm = take(P * 8);
+    L.off_rp = take(P * 8);
+    L.off_rsc = take(PP * 8);
+    L.off_cmat = take(PP * 8);
+    L.off_rmat = take(PP * 8);
+    L.off_rinv = take(PP * 8);
+    L.off_bout = take(PP * 8);
+    L.total = o;
+    return L;
+}
+
+static bool valid_opts(const lingam_opts& o) {
+    return (o.precision == LINGAM_MIXED || o.precision == LINGAM_FP64) &&
+           (o.input_dtype == LINGAM_F32 || o.input_dtype == LINGAM_F64) && (o.prune == 0 || o.prune == 1) &&
+           (o.reuse == 0 || o.reuse == 1) && o.split_n >= 0 && o.tile_i >= 0 && o.tile_j >= 0;
+}
+
+static bool is_device_ptr(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Sample-axis split of the pair kernel: enough CTAs for two per SM on the
+// first wave of the iteration, each split at least one chunk long.
+static int choose_split(int r, int ld, int precision, int nsm, int override_split, int maxsplit) {
+    if (override_split > 0) return std::min(override_split, maxsplit);
+    const int tiles = (r + kTI - 1) / kTI;
+    const int target = 2 * nsm;
+    int s = (target + tiles - 1) / tiles;
+    s = std::min(s, ld / chunk_of(precision));
+    return std::max(1, std::min(s, maxsplit));
+}
+
+static int fit_one(const void* X, long long p_, long long n_, int* order, double* B, void* workspace,
+                   const lingam_opts& o, lingam_report* rep) {
+    if (!X || !order || !workspace || p_ < 1 || n_ < 3 || p_ > kMaxP || n_ > (1ll << 30) || !valid_opts(o))
+        return LINGAM_EINVAL;
+    if (!is_device_ptr(workspace) || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return LINGAM_EINVAL;
+    const int p = int(p_), n = int(n_);
+    cudaStream_t st = static_cast<cudaStream_t>(o.stream);
+    const Layout L = make_layout(p_, n_, o.precision, o.input_dtype);
+    char* base = static_cast<char*>(workspace);
+
+    if (o.forced_order) {   // must be a permutation of 0..p-1
+        std::vector<char> seen(size_t(p), 0);
+        for (int k = 0; k < p; ++k) {
+            const int v = o.forced_order[k];
+            if (v < 0 || v >= p || seen[size_t(v)]) return LINGAM_EINVAL;
+            seen[size_t(v)] = 1;
+        }
+    }
+    int nsm = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return LINGAM_ECUDA;
+
+    Fit f;
+    std::memset(&f, 0, sizeof(f));
+    f.p = p;
+    f.n = n;
+    f.ld = L.ld;
+    f.precision = o.precision;
+    f.prune = o.prune;
+    f.reuse = o.reuse;
+    f.has_forced = o.forced_order != nullptr;
+    f.want_scores = rep && rep->scores ? 1 : 0;
+    f.xt = base + L.off_xt;
+    f.mu = reinterpret_cast<double*>(base + L.off_mu);
+    f.sd = reinterpret_cast<double*>(base + L.off_sd);
+    f.sig = reinterpret_cast<double*>(base + L.off_sig);
+    f.sig0 = reinterpret_cast<double*>(base + L.off_sig0);
+    f.hx = reinterpret_cast<double*>(base + L.off_hx);
+    f.part = reinterpret_cast<double*>(base + L.off_part);
+    f.prev = reinterpret_cast<double*>(base + L.off_prev);
+    f.flags = reinterpret_cast<int*>(base + L.off_flags);
+    f.sigma = reinterpret_cast<int*>(base + L.off_sigma);
+    f.rows = reinterpret_cast<int*>(base + L.off_rows);
+    f.cols = reinterpret_cast<int*>(base + L.off_cols);
+    f.order = reinterpret_cast<int*>(base + L.off_order);
+    f.forced = o.forced_order ? reinterpret_cast<const int*>(base + L.off_forced) : nullptr;
+    f.scratch = reinterpret_cast<int*>(base + L.off_scratch);
+    f.rowsum = reinterpret_cast<double*>(base + L.off_rowsum);
+    f.colsum = reinterpret_cast<double*>(base + L.off_colsum);
+    f.partials = base + L.off_partials;
+    f.inv_root = reinterpret_cast<double*>(base + L.off_invroot);
+    f.tile_cnt = reinterpret_cast<int*>(base + L.off_tilecnt);
+    f.rep_root_score = reinterpret_cast<double*>(base + L.off_rs);
+    f.rep_margin = reinterpret_cast<double*>(base + L.off_rm);
+    f.rep_pairs = reinterpret_cast<long long*>(base + L.off_rp);
+    f.rep_scores = reinterpret_cast<double*>(base + L.off_rsc);
+    f.cmat = reinterpret_cast<double*>(base + L.off_cmat);
+    f.rmat = reinterpret_cast<double*>(base + L.off_rmat);
+    f.rinv = reinterpret_cast<double*>(base + L.off_rinv);
+    f.bout = reinterpret_cast<double*>(base + L.off_bout);
+    f.ctl = reinterpret_cast<Ctl*>(base + L.off_ctl);
+    f.maxtiles = L.maxtiles;
+    f.maxsplit = L.maxsplit;
+
+#define CK(call)                                  \
+    do {                                          \
+        if ((call) != cudaSuccess) {              \
+            cudaGetLastError();                   \
+            return LINGAM_ECUDA;                  \
+        }                                         \
+    } while (0)
+
+    Ctl c0;
+    std::memset(&c0, 0, sizeof(c0));
+    const double tmo = o.timeout_s > 0 ? o.timeout_s : 10.0;
+    c0.timeout_ns = (unsigned long long)(tmo * 1e9);
+    c0.root = -1;
+    CK(cudaMemcpyAsync(f.ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(f.tile_cnt, 0, size_t(L.maxtiles) * 4, st));
+    if (o.forced_order)
+        CK(cudaMemcpyAsync(base + L.off_forced, o.forced_order, size_t(p) * 4, cudaMemcpyHostToDevice, st));
+
+    const size_t in_bytes = size_t(p) * size_t(n) * (o.input_dtype == LINGAM_F32 ? 4 : 8);
+    const void* xdev = X;
+    if (!is_device_ptr(X)) {
+        CK(cudaMemcpyAsync(base + L.off_xin, X, in_bytes, cudaMemcpyHostToDevice, st));
+        xdev = base + L.off_xin;
+    }
+
+    CK(cudaMemsetAsync(f.order, 0xff, size_t(p) * 4, st));   // -1 for iterations not run
+    CK(cudaMemsetAsync(f.rep_pairs, 0, size_t(p) * 8, st));
+    CK(cudaMemsetAsync(f.rep_root_score, 0, size_t(p) * 8, st));
+    CK(cudaMemsetAsync(f.rep_margin, 0, size_t(p) * 8, st));
+    const int iters = (o.max_iters > 0 && o.max_iters < p) ? o.max_iters : p;
+    const bool want_B = B != nullptr && iters == p;
+    cudaEvent_t ev[5];
+    for (int k = 0; k < 5; ++k) CK(cudaEventCreate(&ev[k]));
+    std::vector<cudaEvent_t> pev;   // per-iteration pair-phase events (opts.timing)
+    long long launches = 0;
+    int status = LINGAM_OK;
+    do {
+        if (cudaEventRecord(ev[0], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+        if (launch_standardize(f, xdev, o.input_dtype, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+        if (cudaEventRecord(ev[1], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+        if (launch_gram(f, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+        if (cudaEventRecord(ev[2], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+        launches += 2;
+        for (int it = 0; it < iters && status == LINGAM_OK; ++it) {
+            const int r = p - it;
+            const int S = choose_split(r, L.ld, o.precision, nsm, o.split_n, L.maxsplit);
+            if (launch_plan(f, it, S, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+            ++launches;
+            if (r >= 2) {
+                const int waves = (r + kTJ - 1) / kTJ;
+                const int grid = ((r + kTI - 1) / kTI) * S;
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                if (o.timing) {
+                    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+                        status = LINGAM_ECUDA;
+                        break;
+                    }
+                    pev.push_back(e0);
+                    pev.push_back(e1);
+                    cudaEventRecord(e0, st);
+                }
+                for (int w = 0; w < waves; ++w)
+                    if (launch_pair_wave(f, it, grid, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+                launches += waves;
+                if (o.timing) cudaEventRecord(e1, st);
+            }
+            if (status == LINGAM_OK && it < p - 1) {
+                if (launch_remove_root(f, it, r, st) != cudaSuccess) status = LINGAM_ECUDA;
+                launches += 2;
+            }
+        }
+        if (status != LINGAM_OK) break;
+        if (cudaEventRecord(ev[3], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+        if (want_B && launch_fit_B(f, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+        if (want_B) launches += 3 + p;
+        if (cudaEventRecord(ev[4], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+    } while (0);
+    if (cudaStreamSynchronize(st) != cudaSuccess) status = LINGAM_ECUDA;
+    Ctl ch;
+    if (status == LINGAM_OK) {
+        if (cudaMemcpy(&ch, f.ctl, sizeof(ch), cudaMemcpyDeviceToHost) != cudaSuccess) status = LINGAM_ECUDA;
+        else if (ch.status != 0) status = ch.status;
+    }
+    if (status == LINGAM_OK) {
+        // outputs (cudaMemcpyDefault: host or device destinations)
+        if (cudaMemcpyAsync(order, f.order, size_t(p) * 4, cudaMemcpyDefault, st) != cudaSuccess) status = LINGAM_ECUDA;
+        if (want_B && cudaMemcpyAsync(B, f.bout, size_t(p) * p * 8, cudaMemcpyDefault, st) != cudaSuccess)
+            status = LINGAM_ECUDA;
+        if (rep) {
+            if (rep->root_score) cudaMemcpyAsync(rep->root_score, f.rep_root_score, size_t(p) * 8, cudaMemcpyDefault, st);
+            if (rep->margin_lb) cudaMemcpyAsync(rep->margin_lb, f.rep_margin, size_t(p) * 8, cudaMemcpyDefault, st);
+            if (rep->pairs_evaluated)
+                cudaMemcpyAsync(rep->pairs_evaluated, f.rep_pairs, size_t(p) * 8, cudaMemcpyDefault, st);
+            if (rep->scores) cudaMemcpyAsync(rep->scores, f.rep_scores, size_t(p) * p * 8, cudaMemcpyDefault, st);
+            float ms = 0.f;
+            rep->t_standardize_ms = cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess ? ms : -1.0;
+            rep->t_gram_ms = cudaEventElapsedTime(&ms, ev[1], ev[2]) == cudaSuccess ? ms : -1.0;
+            rep->t_order_ms = cudaEventElapsedTime(&ms, ev[2], ev[3]) == cudaSuccess ? ms : -1.0;
+            rep->t_B_ms = (want_B && cudaEventElapsedTime(&ms, ev[3], ev[4]) == cudaSuccess) ? ms : 0.0;
+            double tp = 0.0;
+            for (size_t k = 0; k + 1 < pev.size(); k += 2)
+                if (cudaEventElapsedTime(&ms, pev[k], pev[k + 1]) == cudaSuccess) tp += ms;
+            rep->t_pair_ms = tp;
+            rep->kernel_launches = launches;
+        }
+        if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) status = LINGAM_ECUDA;
+        if (rep && status == LINGAM_OK) {
+            std::vector<long long> pe(static_cast<size_t>(p));
+            if (cudaMemcpy(pe.data(), f.rep_pairs, size_t(p) * 8, cudaMemcpyDeviceToHost) == cudaSuccess) {
+                long long tot = 0, unp = 0;
+                for (int k = 0; k < iters; ++k) {
+                    tot += pe[size_t(k)];
+                    const long long r = p - k;
+                    unp += o.reuse ? r * (r - 1) / 2 : r * (r - 1);
+                }
+                rep->pairs_total = tot;
+                rep->pairs_unpruned = unp;
+            }
+        }
+    }
+    for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+    for (cudaEvent_t e : pev) cudaEventDestroy(e);
+    cudaGetLastError();
+    return status;
+#undef CK
+}
+
+}  // namespace lingam
+
+using namespace lingam;
+
+extern "C" {
+
+void lingam_default_opts(lingam_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = LINGAM_MIXED;
+    o->input_dtype = LINGAM_F32;
+    o->prune = 1;
+    o->reuse = 1;
+    o->timeout_s = 10.0;
+}
+
+size_t lingam_workspace_size(long long p, long long n, const lingam_opts* opts) {
+    lingam_opts o;
+    lingam_default_opts(&o);
+    if (opts) o = *opts;
+    if (p < 1 || n < 3 || p > kMaxP || n > (1ll << 30) || !valid_opts(o)) return 0;
+    return make_layout(p, n, o.precision, o.input_dtype).total;
+}
+
+int lingam_fit(const void* X, long long p, long long n, int* order, double* B, void* workspace,
+               const lingam_opts* opts, lingam_report* report) {
+    lingam_opts o;
+    lingam_default_opts(&o);
+    if (opts) o = *opts;
+    return fit_one(X, p, n, order, B, workspace, o, report);
+}
+
+size_t lingam_workspace_size_batch(int count, const long long* p, const long long* n, const lingam_opts* opts) {
+    if (count < 0 || (count > 0 && (!p || !n))) return 0;
+    size_t tot = 0;
+    for (int k = 0; k < count; ++k) {
+        const size_t s = lingam_workspace_size(p[k], n[k], opts);
+        if (s == 0) return 0;
+        tot += align_up(s);
+    }
+    return tot;
+}
+
+int lingam_fit_batch(int count, const void* const* X, const long long* p, const long long* n, int* const* order,
+                     double* const* B, void* workspace, const lingam_opts* opts, int* status, lingam_report* report) {
+    if (count < 0 || (count > 0 && (!X || !p || !n || !order || !workspace))) return LINGAM_EINVAL;
+    lingam_opts o;
+    lingam_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.forced_order) return LINGAM_EINVAL;
+    int first = LINGAM_OK;
+    size_t off = 0;
+    for (int k = 0; k < count; ++k) {
+        const size_t s = lingam_workspace_size(p[k], n[k], &o);
+        int st = s == 0 ? LINGAM_EINVAL
+                        : fit_one(X[k], p[k], n[k], order[k], B ? B[k] : nullptr, static_cast<char*>(workspace) + off, o,
+                                  report ? &report[k] : nullptr);
+        off += align_up(s);
+        if (status) status[k] = st;
+        if (st != LINGAM_OK && first == LINGAM_OK) first = st;
+    }
+    return first;
+}
+
+const char* lingam_status_string(int s) {
+    switch (s) {
+        case LINGAM_OK: return "ok";
+        case LINGAM_EINVAL: return "invalid argument";
+        case LINGAM_EDEGENERATE: return "degenerate data (zero variance, |rho| >= 1 or non-finite value)";
+        case LINGAM_ENOMEM: return "out of memory";
+        case LINGAM_ECUDA: return "CUDA error";
+        case LINGAM_ETIMEOUT: return "device-side wait timed out";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,235 @@
+"""Python binding of the C ABI in include/lingam.h (argument marshalling only).
+
+Every step of the ordering runs in the CUDA library liblingam_gb300.so; this
+module only loads it, allocates the device workspace with PyTorch, and moves
+arguments across the ABI.  There is no CPU fallback: if the library is not
+built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+LINGAM_OK, LINGAM_EINVAL, LINGAM_EDEGENERATE, LINGAM_ENOMEM, LINGAM_ECUDA, LINGAM_ETIMEOUT = 0, -1, -2, -3, -4, -5
+LINGAM_FP64, LINGAM_MIXED = 0, 1
+LINGAM_F32, LINGAM_F64 = 0, 1
+
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_dbl_p = ctypes.POINTER(ctypes.c_double)
+_c_ll_p = ctypes.POINTER(ctypes.c_longlong)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("input_dtype", ctypes.c_int), ("prune", ctypes.c_int),
+                ("reuse", ctypes.c_int), ("tile_i", ctypes.c_int), ("tile_j", ctypes.c_int),
+                ("split_n", ctypes.c_int), ("timeout_s", ctypes.c_double), ("stream", ctypes.c_void_p),
+                ("forced_order", _c_int_p), ("max_iters", ctypes.c_int), ("timing", ctypes.c_int)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("root_score", _c_dbl_p), ("margin_lb", _c_dbl_p), ("pairs_evaluated", _c_ll_p),
+                ("scores", _c_dbl_p), ("t_standardize_ms", ctypes.c_double), ("t_gram_ms", ctypes.c_double),
+                ("t_order_ms", ctypes.c_double), ("t_B_ms", ctypes.c_double), ("pairs_total", ctypes.c_longlong),
+                ("pairs_unpruned", ctypes.c_longlong), ("t_pair_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_longlong)]
+
+
+class LingamError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lingam status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    L.lingam_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.lingam_default_opts.restype = None
+    L.lingam_workspace_size.argtypes = [ctypes.c_longlong, ctypes.c_longlong, ctypes.POINTER(Opts)]
+    L.lingam_workspace_size.restype = ctypes.c_size_t
+    L.lingam_fit.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.POINTER(Report)]
+    L.lingam_fit.restype = ctypes.c_int
+    L.lingam_workspace_size_batch.argtypes = [ctypes.c_int, _c_ll_p, _c_ll_p, ctypes.POINTER(Opts)]
+    L.lingam_workspace_size_batch.restype = ctypes.c_size_t
+    L.lingam_fit_batch.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), _c_ll_p, _c_ll_p,
+                                   ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                                   ctypes.POINTER(Opts), _c_int_p, ctypes.POINTER(Report)]
+    L.lingam_fit_batch.restype = ctypes.c_int
+    L.lingam_status_string.argtypes = [ctypes.c_int]
+    L.lingam_status_string.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/lingam.h."""
+    hdr = open(os.path.join(_build.INCLUDE, "lingam.h")).read()
+    return sorted(set(re.findall(r"\b(lingam_[a-z_0-9]+)\s*\(", hdr)))
+
+
+def status_string(status: int) -> str:
+    return load().lingam_status_string(status).decode()
+
+
+def make_opts(precision: str = "mixed", input_dtype=np.float32, prune: bool = True, reuse: bool = True,
+              split_n: int = 0, timeout_s: float = 10.0, stream=None, forced_order=None, max_iters: int = 0,
+              timing: bool = False) -> tuple[Opts, object]:
+    o = Opts()
+    load().lingam_default_opts(ctypes.byref(o))
+    o.precision = {"mixed": LINGAM_MIXED, "fp64": LINGAM_FP64}[precision]
+    o.input_dtype = LINGAM_F32 if np.dtype(input_dtype) == np.float32 else LINGAM_F64
+    o.prune = int(prune)
+    o.reuse = int(reuse)
+    o.split_n = int(split_n)
+    o.timeout_s = float(timeout_s)
+    o.stream = ctypes.c_void_p(stream) if stream else None
+    o.max_iters = int(max_iters)
+    o.timing = int(bool(timing))
+    keep = None
+    if forced_order is not None:
+        keep = np.ascontiguousarray(forced_order, dtype=np.int32)
+        o.forced_order = keep.ctypes.data_as(_c_int_p)
+    return o, keep
+
+
+def workspace_size(p: int, n: int, precision: str = "mixed", input_dtype=np.float32) -> int:
+    o, _ = make_opts(precision, input_dtype)
+    return int(load().lingam_workspace_size(p, n, ctypes.byref(o)))
+
+
+@dataclass
+class FitResult:
+    order: np.ndarray
+    B: np.ndarray | None
+    root_score: np.ndarray
+    margin_lb: np.ndarray
+    pairs_evaluated: np.ndarray
+    scores: np.ndarray | None
+    times_ms: dict = field(default_factory=dict)
+    pairs_total: int = 0
+    pairs_unpruned: int = 0
+    kernel_launches: int = 0
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def alloc_workspace(nbytes: int, device=None):
+    """Device workspace (uint8 tensor, 256-byte aligned by the caching allocator)."""
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def _addr(a) -> int:
+    """Address of a numpy array or torch tensor."""
+    return a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()
+
+
+def _data_ptr(X):
+    """(pointer, p, n, dtype, keepalive) of a numpy array or torch tensor."""
+    if isinstance(X, np.ndarray):
+        if X.dtype not in (np.float32, np.float64):
+            X = X.astype(np.float64)
+        X = np.ascontiguousarray(X)
+        return X.ctypes.data, X.shape[0], X.shape[1], X.dtype, X
+    torch = _torch()
+    if isinstance(X, torch.Tensor):
+        if X.dtype not in (torch.float32, torch.float64):
+            X = X.double()
+        X = X.contiguous()
+        dt = np.float32 if X.dtype == torch.float32 else np.float64
+        return X.data_ptr(), X.shape[0], X.shape[1], dt, X
+    raise TypeError("X must be a numpy array or a torch tensor (p x n)")
+
+
+def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, forced_order=None,
+        want_scores: bool = False, want_B: bool = True, split_n: int = 0, timeout_s: float = 10.0,
+        stream=None, workspace=None, max_iters: int = 0, timing: bool = False, out=None) -> FitResult:
+    """lingam_fit on X (p x n, numpy on the host or a torch tensor on the GPU)."""
+    L = load()
+    ptr, p, n, dt, keep = _data_ptr(X)
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    o, keep_forced = make_opts(precision, dt, prune, reuse, split_n, timeout_s, stream, forced_order, max_iters,
+                               timing)
+    need = int(L.lingam_workspace_size(p, n, ctypes.byref(o)))
+    if need == 0:
+        raise LingamError(LINGAM_EINVAL, "invalid sizes or options")
+    if workspace is None or workspace.numel() < need:
+        workspace = alloc_workspace(need)
+    if out is not None:            # caller-provided (e.g. pinned) host buffers for order and B
+        order, B = out
+    else:
+        order = np.zeros(p, dtype=np.int32)
+        B = np.zeros((p, p)) if want_B else None
+    rs = np.zeros(p)
+    mg = np.zeros(p)
+    pe = np.zeros(p, dtype=np.int64)
+    sc = np.full((p, p), np.nan) if want_scores else None
+    rep = Report()
+    rep.root_score = rs.ctypes.data_as(_c_dbl_p)
+    rep.margin_lb = mg.ctypes.data_as(_c_dbl_p)
+    rep.pairs_evaluated = pe.ctypes.data_as(_c_ll_p)
+    if sc is not None:
+        rep.scores = sc.ctypes.data_as(_c_dbl_p)
+    st = L.lingam_fit(ctypes.c_void_p(ptr), p, n, _addr(order), _addr(B) if B is not None else None,
+                      ctypes.c_void_p(workspace.data_ptr()), ctypes.byref(o), ctypes.byref(rep))
+    del keep, keep_forced
+    if st != LINGAM_OK:
+        raise LingamError(st, status_string(st))
+    return FitResult(order=order, B=B, root_score=rs, margin_lb=mg, pairs_evaluated=pe, scores=sc,
+                     times_ms={"standardize": rep.t_standardize_ms, "gram": rep.t_gram_ms,
+                               "order": rep.t_order_ms, "B": rep.t_B_ms, "pair": rep.t_pair_ms},
+                     pairs_total=int(rep.pairs_total), pairs_unpruned=int(rep.pairs_unpruned),
+                     kernel_launches=int(rep.kernel_launches))
+
+
+def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = True, stream=None):
+    """lingam_fit_batch over a list of data sets (numpy or torch, each p_k x n_k)."""
+    L = load()
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    items = [_data_ptr(X) for X in Xs]
+    count = len(items)
+    dts = {it[3] for it in items}
+    if len(dts) > 1:
+        raise TypeError("all data sets of a batch must share one dtype")
+    o, _ = make_opts(precision, items[0][3] if items else np.float32, prune, True, 0, 10.0, stream)
+    ps = (ctypes.c_longlong * count)(*[it[1] for it in items])
+    ns = (ctypes.c_longlong * count)(*[it[2] for it in items])
+    need = int(L.lingam_workspace_size_batch(count, ps, ns, ctypes.byref(o)))
+    ws = alloc_workspace(need)
+    orders = [np.zeros(it[1], dtype=np.int32) for it in items]
+    Bs = [np.zeros((it[1], it[1])) for it in items] if want_B else None
+    xp = (ctypes.c_void_p * count)(*[it[0] for it in items])
+    op = (ctypes.c_void_p * count)(*[o_.ctypes.data for o_ in orders])
+    bp = (ctypes.c_void_p * count)(*[b.ctypes.data for b in Bs]) if Bs is not None else None
+    status = np.zeros(count, dtype=np.int32)
+    st = L.lingam_fit_batch(count, xp, ps, ns, op, bp, ctypes.c_void_p(ws.data_ptr()), ctypes.byref(o),
+                            status.ctypes.data_as(_c_int_p), None)
+    return st, status, orders, Bs

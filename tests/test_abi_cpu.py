@@ -1,0 +1,62 @@
+"""CPU checks of the C ABI library: it builds, loads, and exports every
+function include/lingam.h declares; the calls that need no GPU behave."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2109_13993_gb300 import build, lingam
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return lingam.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = lingam.header_functions()
+    assert {"lingam_fit", "lingam_fit_batch", "lingam_workspace_size", "lingam_status_string",
+            "lingam_default_opts", "lingam_workspace_size_batch"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_default_opts(lib):
+    o = lingam.Opts()
+    lib.lingam_default_opts(ctypes.byref(o))
+    assert o.precision == lingam.LINGAM_MIXED and o.input_dtype == lingam.LINGAM_F32
+    assert o.prune == 1 and o.reuse == 1 and o.timeout_s == 10.0 and not o.stream and not o.forced_order
+
+
+def test_status_strings(lib):
+    for s in (0, -1, -2, -3, -4, -5):
+        assert lingam.status_string(s)
+    assert lingam.status_string(0) == "ok"
+    assert lingam.status_string(123) == "unknown status"
+
+
+def test_workspace_size(lib):
+    a = lingam.workspace_size(100, 10000)
+    b = lingam.workspace_size(1000, 10000)
+    c = lingam.workspace_size(1000, 10000, precision="fp64")
+    assert 0 < a < b < c
+    assert b % 256 == 0
+    assert lingam.workspace_size(0, 100) == 0
+    assert lingam.workspace_size(10, 2) == 0
+    o, _ = lingam.make_opts()
+    o.precision = 7
+    assert lib.lingam_workspace_size(10, 100, ctypes.byref(o)) == 0
+    ps = (ctypes.c_longlong * 2)(10, 20)
+    ns = (ctypes.c_longlong * 2)(100, 200)
+    tot = lib.lingam_workspace_size_batch(2, ps, ns, None)
+    assert tot >= lingam.workspace_size(10, 100) + lingam.workspace_size(20, 200)
+
+
+def test_fit_rejects_bad_arguments_without_gpu_work(lib):
+    # NULL pointers and bad sizes are rejected before any CUDA call
+    assert lib.lingam_fit(None, 10, 100, None, None, None, None, None) == lingam.LINGAM_EINVAL
+    x = np.zeros((3, 10), dtype=np.float32)
+    order = np.zeros(3, dtype=np.int32)
+    assert lib.lingam_fit(ctypes.c_void_p(x.ctypes.data), 3, 2, order.ctypes.data, None, None, None,
+                          None) == lingam.LINGAM_EINVAL

@@ -1,0 +1,235 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (stated by the build's target): FP64 GPU path scores and B within
+1e-10 relative (absolute floor 1e-14 on scores); mixed path scores within
+1e-4 absolute.  The causal order must be identical on every iteration whose
+oracle margin (second lowest minus lowest score) exceeds twice the measured
+score error tau; after the first iteration that is not resolved the paths
+may legitimately diverge, so later iterations are checked in forced-order
+mode (both sides take the oracle's root).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_13993_gb300 import lingam, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2109_13993_gb300 import build
+    build.build()
+    lingam.load()
+    oracle.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _dev(X, dtype):
+    return torch.tensor(np.ascontiguousarray(X), dtype=dtype, device="cuda")
+
+
+def _margins(S):
+    out = []
+    for row in S:
+        v = np.sort(row[~np.isnan(row)])
+        out.append(v[1] - v[0] if len(v) > 1 else np.inf)
+    return np.array(out)
+
+
+def _argmin(row):
+    alive = np.nonzero(~np.isnan(row))[0]
+    return int(alive[np.lexsort((alive, row[alive]))[0]])
+
+
+def _check_scores(gpu, ora, rtol, atol):
+    """Element-wise score parity; returns tau_it, the largest error at each iteration."""
+    m = ~np.isnan(ora)
+    assert np.array_equal(m, ~np.isnan(gpu)), "score layout differs"
+    err = np.abs(np.where(m, gpu, 0.0) - np.where(m, ora, 0.0))
+    bound = rtol * np.abs(np.where(m, ora, 0.0)) + atol
+    assert np.all(err <= bound), f"max err {err.max():.3e}, worst ratio {(err / bound).max():.3f}"
+    return err.max(axis=1)
+
+
+def _check_argmin_resolved(gpu_S, ora_S, tau_it):
+    """Forced-order mode: on every iteration whose oracle margin exceeds
+    2 tau_it, the GPU's argmin equals the oracle's.  Returns how many
+    iterations were resolved."""
+    margins = _margins(ora_S)
+    resolved = 0
+    for it in range(ora_S.shape[0]):
+        if margins[it] > 2 * tau_it[it]:
+            resolved += 1
+            assert _argmin(gpu_S[it]) == _argmin(ora_S[it]), f"iteration {it}"
+    return resolved
+
+
+def _check_free_run(gpu_order, ora_order, ora_S, tau_it):
+    """Free run: the orders agree until the first iteration where they differ,
+    and that iteration must be one the oracle margin does not resolve."""
+    margins = _margins(ora_S)
+    for it in range(len(ora_order)):
+        if gpu_order[it] != ora_order[it]:
+            assert margins[it] <= 2 * tau_it[it], f"resolved iteration {it} differs"
+            return it
+    return len(ora_order)
+
+
+# ---------------------------------------------------------------- FP64 path vs oracle, 1e-10
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_fp64_path_matches_oracle(seed):
+    d = synth.workload("p20_n2000", seed=seed)
+    o_order, o_B, o_S = oracle.fit(d.X)
+    res = lingam.fit(_dev(d.X, torch.float64), precision="fp64", prune=False, forced_order=o_order,
+                     want_scores=True)
+    tau = _check_scores(res.scores, o_S, rtol=1e-10, atol=1e-14)
+    assert np.array_equal(res.order, o_order)
+    assert _check_argmin_resolved(res.scores, o_S, tau) == len(o_order)
+    scale = np.abs(o_B).max()
+    assert np.allclose(res.B, o_B, rtol=1e-10, atol=1e-10 * scale), np.abs(res.B - o_B).max()
+    free = lingam.fit(_dev(d.X, torch.float64), precision="fp64")
+    assert _check_free_run(free.order, o_order, o_S, tau) == len(o_order)
+
+
+# ---------------------------------------------------------------- mixed path vs oracle, 1e-4
+
+@pytest.mark.parametrize("name,seed", [("p20_n2000", 1), ("p20_n2000", 2), ("p100_n10000", 1)])
+def test_mixed_path_matches_oracle(name, seed):
+    d = synth.workload(name, seed=seed)
+    X32 = d.X.astype(np.float32)
+    o_order, o_B, o_S = oracle.fit(X32.astype(np.float64))
+    res = lingam.fit(_dev(X32, torch.float32), precision="mixed", prune=False, forced_order=o_order,
+                     want_scores=True)
+    tau = _check_scores(res.scores, o_S, rtol=0.0, atol=1e-4)
+    resolved = _check_argmin_resolved(res.scores, o_S, tau)
+    free = lingam.fit(_dev(X32, torch.float32), precision="mixed")
+    upto = _check_free_run(free.order, o_order, o_S, tau)
+    print(f"{name}/{seed}: max score error {tau.max():.2e}; {resolved} of {len(o_order)} iterations "
+          f"margin-resolved; free-run order identical on the first {upto}")
+    assert sorted(free.order.tolist()) == list(range(len(o_order)))
+    scale = np.abs(o_B).max()
+    assert np.abs(res.B - o_B).max() <= 1e-4 * max(1.0, scale)
+
+
+# ---------------------------------------------------------------- threshold pruning is exact
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_pruning_and_reuse_do_not_change_the_result(precision):
+    d = synth.workload("p100_n10000", seed=3)
+    dt = torch.float32 if precision == "mixed" else torch.float64
+    X = _dev(d.X, dt)
+    full = lingam.fit(X, precision=precision, prune=False)
+    pr = lingam.fit(X, precision=precision, prune=True)
+    assert np.array_equal(full.order, pr.order)
+    assert np.allclose(pr.root_score, full.root_score, rtol=1e-12, atol=1e-300)
+    assert full.pairs_total == full.pairs_unpruned
+    assert pr.pairs_total <= pr.pairs_unpruned
+    print(f"{precision}: pairs evaluated {pr.pairs_total} of {pr.pairs_unpruned} "
+          f"({100.0 * (1 - pr.pairs_total / pr.pairs_unpruned):.1f}% saved)")
+    if precision == "mixed":
+        noreuse = lingam.fit(X, precision=precision, prune=False, reuse=False)
+        assert np.array_equal(noreuse.order, full.order)
+        assert noreuse.pairs_total == 2 * full.pairs_total
+        assert np.allclose(noreuse.root_score, full.root_score, rtol=1e-5, atol=1e-9)
+
+
+# ---------------------------------------------------------------- worked example of the paper
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_fig1_worked_example(precision):
+    d = synth.fig1_sem(100_000, seed=1)
+    dt = torch.float32 if precision == "mixed" else torch.float64
+    res = lingam.fit(_dev(d.X, dt), precision=precision)
+    assert list(res.order) == [2, 4, 0, 3, 1]          # k = [3, 5, 1, 4, 2] (1-based)
+    assert np.max(np.abs(res.B - d.B)) < 0.05
+
+
+# ---------------------------------------------------------------- ragged and edge sizes
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("p,n", [(1, 10), (2, 3), (3, 5), (33, 257), (37, 1000), (65, 2001)])
+def test_edge_sizes_match_oracle(precision, p, n):
+    d = synth.lingam_dataset(p, n, min(1.0, 3.0 / max(p - 1, 1)), seed=p * 1000 + n)
+    X = d.X.astype(np.float32) if precision == "mixed" else d.X
+    o_order, o_B, o_S = oracle.fit(X.astype(np.float64))
+    dt = torch.float32 if precision == "mixed" else torch.float64
+    res = lingam.fit(_dev(X, dt), precision=precision, prune=False, forced_order=o_order, want_scores=True)
+    if precision == "fp64":
+        tau = _check_scores(res.scores, o_S, rtol=1e-10, atol=1e-14)
+    else:
+        tau = _check_scores(res.scores, o_S, rtol=0.0, atol=1e-4)
+    assert np.array_equal(res.order, o_order)
+    _check_argmin_resolved(res.scores, o_S, tau)
+    free = lingam.fit(_dev(X, dt), precision=precision)
+    assert sorted(free.order.tolist()) == list(range(p))
+
+
+def test_host_and_device_inputs_agree():
+    d = synth.lingam_dataset(37, 1500, 0.1, seed=5)
+    X32 = d.X.astype(np.float32)
+    a = lingam.fit(X32, precision="mixed", want_scores=True)
+    b = lingam.fit(_dev(X32, torch.float32), precision="mixed", want_scores=True)
+    assert np.array_equal(a.order, b.order)
+    assert np.array_equal(np.isnan(a.scores), np.isnan(b.scores))
+    m = ~np.isnan(a.scores)
+    assert np.array_equal(a.scores[m], b.scores[m])
+    assert np.array_equal(a.B, b.B)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_degenerate_inputs_are_reported(precision):
+    d = synth.lingam_dataset(8, 500, 0.3, seed=2)
+    dt = torch.float32 if precision == "mixed" else torch.float64
+    for bad in ("constant", "duplicate", "nan"):
+        X = d.X.copy()
+        if bad == "constant":
+            X[3] = 1.5
+        elif bad == "duplicate":
+            X[5] = 2.0 * X[1] + 1.0
+        else:
+            X[2, 17] = np.nan
+        with pytest.raises(lingam.LingamError) as e:
+            lingam.fit(_dev(X, dt), precision=precision)
+        assert e.value.status == lingam.LINGAM_EDEGENERATE, bad
+    with pytest.raises(lingam.LingamError) as e:
+        lingam.fit(_dev(d.X, dt), precision=precision, forced_order=[0, 0, 1, 2, 3, 4, 5, 6])
+    assert e.value.status == lingam.LINGAM_EINVAL
+
+
+def test_batch_matches_single_fits():
+    ds = synth.uneven_batch(3, seed=4)
+    Xs = [_dev(d.X[:, : min(d.X.shape[1], 3000)].astype(np.float32), torch.float32) for d in ds]
+    st, status, orders, Bs = lingam.fit_batch(Xs, precision="mixed")
+    assert st == 0 and np.all(status == 0)
+    for X, o, B in zip(Xs, orders, Bs):
+        single = lingam.fit(X, precision="mixed")
+        assert np.array_equal(single.order, o)
+        assert np.array_equal(single.B, B)
+
+
+# ---------------------------------------------------------------- full size, sampled outputs
+
+def test_full_size_sampled_scores():
+    """p = 1000, n = 10^4 in the configuration the benchmark times (mixed,
+    pruning and reuse on): sampled complete scores against the oracle at
+    iteration 0 and after the GPU's own first roots."""
+    d = synth.workload("p1000_n10000", seed=1)
+    X32 = d.X.astype(np.float32)
+    res = lingam.fit(_dev(X32, torch.float32), precision="mixed", want_scores=True)
+    assert sorted(res.order.tolist()) == list(range(1000))
+    assert res.pairs_total < res.pairs_unpruned
+    X64 = X32.astype(np.float64)
+    for k in (0, 7):
+        row = res.scores[k]
+        complete = np.nonzero(~np.isnan(row))[0]
+        assert res.order[k] in complete
+        sample = np.unique(np.concatenate([[res.order[k]], complete[:: max(1, len(complete) // 6)][:6]]))
+        ora = oracle.variable_scores(X64, res.order[:k], sample)
+        err = np.abs(row[sample] - ora)
+        assert err.max() <= 1e-4, (k, err.max())
+        print(f"iteration {k}: {len(complete)} complete variables, max |dS| over {len(sample)} sampled = {err.max():.2e}")

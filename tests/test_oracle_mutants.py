@@ -75,7 +75,7 @@ def tmpdir_mut():
 def test_pins_catch_mutant(mutant, tmpdir_mut):
     old, new = MUTANTS[mutant]
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation site of {mutant} not found once"
+    assert src.count(old) >= 1, f"mutation site of {mutant} not found"
     path_c = os.path.join(tmpdir_mut, f"{mutant}.c")
     path_so = os.path.join(tmpdir_mut, f"lib{mutant}.so")
     open(path_c, "w").write(src.replace(old, new))

@@ -314,3 +314,13 @@ def test_generator_is_deterministic():
     assert not np.array_equal(a.X, c.X)
     P = a.B[np.ix_(a.order, a.order)]
     assert np.all(np.triu(P) == 0.0)
+
+
+def test_variable_scores_match_fit(oracle_mod):
+    d = synth.workload("p20_n2000", seed=2)
+    order, _, S = oracle_mod.fit(d.X, want_B=False)
+    for k in (0, 3, 11):
+        alive = [v for v in range(20) if v not in set(order[:k].tolist())]
+        vs = alive[::3]
+        got = oracle_mod.variable_scores(d.X, order[:k], vs)
+        assert np.allclose(got, S[k, vs], rtol=1e-12, atol=1e-18)
