@@ -129,6 +129,33 @@ int lingam_fit_batch(int count, const void* const* X, const long long* p, const 
                      double* const* B, void* workspace, const lingam_opts* opts, int* status,
                      lingam_report* report);
 
+/*
+ * lingam_fit_static -- lingam_fit for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that have no way to provide the device workspace lingam_fit needs: a plain
+ * host program without a device allocator of its own, a plug-in inside an
+ * application whose memory pool owns the GPU, or a code path where calling
+ * the CUDA allocator is not allowed.  It computes exactly what lingam_fit
+ * computes, with the same arguments minus the workspace, in a scratch array
+ * of LINGAM_STATIC_SCRATCH_BYTES that the library holds on every GPU it is
+ * loaded on until the process exits.  It allocates nothing.
+ *
+ *   - Returns LINGAM_EINVAL when lingam_workspace_size(p, n, opts) exceeds
+ *     LINGAM_STATIC_SCRATCH_BYTES (32 MiB: enough for the mixed path up to
+ *     about p = 200, n = 10^4, or the FP64 path up to about p = 128, n = 10^4).
+ *   - The first call on a device looks up the scratch array's device address
+ *     (once per device, with that device current); make that first call before
+ *     any stream capture on the device.
+ *   - Every call on a device uses the same scratch array and leaves its
+ *     contents behind; each call initialises what it needs.  Calls whose GPU
+ *     work overlaps (several host threads, or several streams) race on the
+ *     array: serialise them.
+ */
+#define LINGAM_STATIC_SCRATCH_BYTES (32u << 20)
+int lingam_fit_static(const void* X, long long p, long long n, int* order, double* B, const lingam_opts* opts,
+                      lingam_report* report);
+
 /* Static, human-readable name of a status code. */
 const char* lingam_status_string(int status);
 

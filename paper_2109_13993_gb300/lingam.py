@@ -76,6 +76,9 @@ def load():
                                    ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
                                    ctypes.POINTER(Opts), _c_int_p, ctypes.POINTER(Report)]
     L.lingam_fit_batch.restype = ctypes.c_int
+    L.lingam_fit_static.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.POINTER(Report)]
+    L.lingam_fit_static.restype = ctypes.c_int
     L.lingam_status_string.argtypes = [ctypes.c_int]
     L.lingam_status_string.restype = ctypes.c_char_p
     _lib = L
@@ -233,3 +236,43 @@ def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = T
     st = L.lingam_fit_batch(count, xp, ps, ns, op, bp, ctypes.c_void_p(ws.data_ptr()), ctypes.byref(o),
                             status.ctypes.data_as(_c_int_p), None)
     return st, status, orders, Bs
+
+
+STATIC_SCRATCH_BYTES = 32 << 20   # LINGAM_STATIC_SCRATCH_BYTES in include/lingam.h
+
+
+def fit_static(X, precision: str = "mixed", prune: bool = True, want_B: bool = True, want_scores: bool = False,
+               stream=None) -> FitResult:
+    """lingam_fit_static: the same fit as `fit`, run in the library's own
+    fixed scratch area instead of a caller-provided workspace, for callers
+    that cannot allocate device memory.  Raises LingamError(EINVAL) when the
+    problem's workspace would exceed STATIC_SCRATCH_BYTES."""
+    L = load()
+    ptr, p, n, dt, keep = _data_ptr(X)
+    if stream is None:
+        stream = _torch().cuda.current_stream().cuda_stream
+    o, _ = make_opts(precision, dt, prune, True, 0, 10.0, stream)
+    order = np.zeros(p, dtype=np.int32)
+    B = np.zeros((p, p)) if want_B else None
+    rs, mg, pe = np.zeros(p), np.zeros(p), np.zeros(p, dtype=np.int64)
+    sc = np.full((p, p), np.nan) if want_scores else None
+    rep = Report()
+    rep.root_score = rs.ctypes.data_as(_c_dbl_p)
+    rep.margin_lb = mg.ctypes.data_as(_c_dbl_p)
+    rep.pairs_evaluated = pe.ctypes.data_as(_c_ll_p)
+    if sc is not None:
+        rep.scores = sc.ctypes.data_as(_c_dbl_p)
+    st = L.lingam_fit_static(ctypes.c_void_p(ptr), p, n, order.ctypes.data, B.ctypes.data if B is not None else None,
+                             ctypes.byref(o), ctypes.byref(rep))
+    del keep
+    if st != LINGAM_OK:
+        need = int(L.lingam_workspace_size(p, n, ctypes.byref(o)))
+        msg = status_string(st)
+        if st == LINGAM_EINVAL and need > STATIC_SCRATCH_BYTES:
+            msg = f"problem needs {need} bytes of scratch, the static area holds {STATIC_SCRATCH_BYTES}"
+        raise LingamError(st, msg)
+    return FitResult(order=order, B=B, root_score=rs, margin_lb=mg, pairs_evaluated=pe, scores=sc,
+                     times_ms={"standardize": rep.t_standardize_ms, "gram": rep.t_gram_ms,
+                               "order": rep.t_order_ms, "B": rep.t_B_ms, "pair": rep.t_pair_ms},
+                     pairs_total=int(rep.pairs_total), pairs_unpruned=int(rep.pairs_unpruned),
+                     kernel_launches=int(rep.kernel_launches))
