@@ -40,6 +40,28 @@ def unpruned_pair_samples(p: int, n: int) -> float:
     return float(sum(r * (r - 1) // 2 for r in range(2, p + 1))) * n
 
 
+def dataset_seed(rank: int) -> int:
+    """Every rank fits its own independent dataset (weak scaling)."""
+    return 1 + rank
+
+
+def shard(count: int, world: int, rank: int) -> list[int]:
+    """Datasets of a batch owned by `rank`: a contiguous, balanced block."""
+    lo = count * rank // world
+    hi = count * (rank + 1) // world
+    return list(range(lo, hi))
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """Largest value over all ranks (the job takes as long as its slowest rank)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks() -> dict:
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -167,8 +189,9 @@ def run_ours(args, rank: int, world: int):
         dist.init_process_group("nccl", device_id=dev)
     entry.build()
     p, n = args.p, args.n
-    d = synth.workload("p1000_n10000", seed=1 + rank) if (p, n) == (P_DEFAULT, N_DEFAULT) else \
-        synth.lingam_dataset(p, n, 4.0 / max(p - 1, 1), seed=1 + rank)
+    seed = dataset_seed(rank)
+    d = synth.workload("p1000_n10000", seed=seed) if (p, n) == (P_DEFAULT, N_DEFAULT) else \
+        synth.lingam_dataset(p, n, 4.0 / max(p - 1, 1), seed=seed)
     X = torch.tensor(d.X.astype(np.float32), device=dev)
     ws = lingam.alloc_workspace(lingam.workspace_size(p, n), device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -180,7 +203,8 @@ def run_ours(args, rank: int, world: int):
         torch.cuda.synchronize(dev)
 
     def step(inp, out=None):
-        return lingam.fit(inp, precision="mixed", workspace=ws, timing=True, out=out)
+        return lingam.fit(inp, precision="mixed", workspace=ws, timing=True, out=out, max_iters=args.max_iters,
+                          want_B=args.max_iters == 0)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -204,13 +228,10 @@ def run_ours(args, rank: int, world: int):
             launches.append(res.kernel_launches)
     clocks = clk.summary()
     barrier()
-    tot_ms = float(np.sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(float(np.sum(step_ms)), dist, dev)
     ms_per_step = tot_ms / args.steps
-    work = unpruned_pair_samples(p, n)
+    work = unpruned_pair_samples(p, n) if args.max_iters == 0 else \
+        float(sum(r * (r - 1) // 2 for r in range(p - args.max_iters + 1, p + 1))) * n
     value = world * work / (ms_per_step / 1000.0)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
@@ -218,7 +239,7 @@ def run_ours(args, rank: int, world: int):
     order_h = torch.empty(p, dtype=torch.int32).pin_memory()
     B_h = torch.empty((p, p), dtype=torch.float64).pin_memory()
     e2e_ms = []
-    for k in range(args.warmup + args.steps):
+    for k in range(0 if args.no_e2e else args.warmup + args.steps):
         flush.zero_()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -228,11 +249,7 @@ def run_ours(args, rank: int, world: int):
         torch.cuda.synchronize(dev)
         if k >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_tot = float(np.sum(e2e_ms))
-    if dist is not None:
-        t = torch.tensor([e2e_tot], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = float(t.item())
+    e2e_tot = max_over_ranks(float(np.sum(e2e_ms)) if e2e_ms else float("nan"), dist, dev)
     e2e_value = world * work / (e2e_tot / args.steps / 1000.0)
 
     # pair-kernel roofline (SFU bound), from the timed steps
@@ -300,6 +317,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
+    ap.add_argument("--max-iters", type=int, default=0, help="order only the first k iterations (profiling)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -86,6 +86,8 @@ typedef struct {
     long long pairs_unpruned;    /* sum over iterations of r(r-1)/2 (r(r-1) when reuse = 0) */
     double t_pair_ms;            /* device time of the pair-comparison launches (opts.timing = 1), else 0 */
     long long kernel_launches;   /* kernels this call launched */
+    double* t_pair_iter_ms;      /* NULL or a HOST array [p]: with opts.timing = 1, device time of the
+                                    pair comparison of iteration k (iterations with r >= 2) */
 } lingam_report;
 
 /* Fills *opts with the defaults: MIXED, F32, prune = reuse = 1, autotuned

@@ -19,11 +19,13 @@ constexpr double kBeta = 0.37457;
 constexpr double kLn2 = 0.69314718055994530942;
 constexpr double kLog2e = 1.44269504088896340736;
 
-// Pair-tile geometry of the FP32 pair kernel: a CTA owns TI rows x TJ columns
-// of the pair matrix; each thread owns 2 rows x 2 columns.
+// Pair tiles: a wave has up to kTJ columns; a tile has kTI (FP64 path) or
+// 2 kTI (FP32 path) rows; kPairThreads bounds the consumer threads of a CTA.
 constexpr int kTI = 32;
 constexpr int kTJ = 32;
-constexpr int kPairThreads = 256;
+constexpr int kPairThreads = 512;
+// Rows of a pair tile for a precision (64 for the FP32 path, 32 for FP64).
+__host__ __device__ __forceinline__ int pair_tile_rows(int precision) { return precision == LINGAM_MIXED ? 64 : 32; }
 constexpr int kChunk = 128;            // samples per shared-memory stage (FP32 path)
 constexpr int kChunk64 = 64;           // samples per stage (FP64 path)
 constexpr int kSub = 32;               // samples per product group (one lg2 per group)
@@ -55,9 +57,13 @@ struct Ctl {
     int ncolumned;       // variables that have been a column this iteration
     double best;         // lowest complete score so far this iteration
     int best_var;        // variable holding `best`
-    int pad0;
+    int merged;          // tiles of the current wave merged so far
     long long pairs_it;  // pairs evaluated this iteration
     unsigned long long timeout_ns;  // bound on device-side waits
+    int bar_count;       // grid barrier: CTAs arrived
+    int bar_gen;         // grid barrier: generation
+    int abort;           // set when a CTA gives up a wait; the others then leave too
+    int pad1;
 };
 
 // Device pointers of one fit, carved out of the caller's workspace.
@@ -89,7 +95,8 @@ struct Fit {
     double* colsum;      // [maxtiles x kTJ] per tile and column: sum over the tile's rows of max(0, I)^2
     void* partials;      // [maxtiles x maxsplit x kPairThreads x 16] split partial moments (float or double)
     double* inv_root;    // [p] 1/sqrt(1 - Sigma[w,root]^2) of the current removal
-    int* tile_cnt;       // [maxtiles] split arrival counters
+    int* tile_cnt;       // [maxtiles] per-tile completion counters
+    void* ibuf;          // [maxtiles x 64 x kTJ] I of the current wave's pairs (float or double)
     double* rep_root_score;  // [p]
     double* rep_margin;      // [p]
     long long* rep_pairs;    // [p]
@@ -163,6 +170,22 @@ __device__ __forceinline__ int block_scan01(int flag, int* red, int* total) {
     }
     *total = tot;
     return off + pre;
+}
+
+// Adds (log cosh u - beta) and u e^{-u^2/2} of one normalised sample u (Eq. HApp)
+// to a thread's running sums; FP32 on the SFU with
+//   log cosh u = |u| + ln2 * log2(1 + 2^{-2 log2(e) |u|}) - ln 2,
+// FP64 with the library exp and log1p.
+__device__ __forceinline__ void mom_add(float u, float& lcc, float& g) {
+    const float au = fabsf(u);
+    const float e = ex2_approx(au * float(-2.0 * kLog2e));
+    lcc += (au + float(kLn2) * lg2_approx(1.f + e)) - float(kLn2 + kBeta);
+    g = fmaf(u, ex2_approx(u * u * float(-0.5 * kLog2e)), g);
+}
+__device__ __forceinline__ void mom_add(double u, double& lcc, double& g) {
+    const double au = fabs(u);
+    lcc += (au + log1p(exp(-2.0 * au))) - (kLn2 + kBeta);
+    g = fma(u, exp(-0.5 * u * u), g);
 }
 
 // Entropy term of Eq. HApp minus H(nu), from the centred sums

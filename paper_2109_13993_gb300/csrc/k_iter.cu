@@ -1,0 +1,1055 @@
+// k_iter.cu -- one iteration of the ordering loop (Algorithm 3) as one
+// persistent kernel: ParaFindRoot (Algorithm 4) as a sequence of pair "waves",
+// then UpdateData (Algorithm 7) and UpdateCovMat (Algorithm 8).  The grid has
+// one CTA per SM and is launched cooperatively, so the phases are separated by
+// grid barriers instead of kernel launches.
+//
+// Phases of an iteration:
+//   plan     (CTA 0) candidate order sigma of the remaining variables U, sorted
+//            by the previous iteration's scores (iteration 0: H(x) - H(nu), most
+//            non-Gaussian first); the first wave's columns are its first kTJ.
+//   waves    repeat until no live candidate is left:
+//     compute  every CTA evaluates its share of the wave's (tile, chunk) units
+//              and writes partial sample moments;
+//     merge    the tiles are spread over the CTAs; each sums its tile's partials
+//              in a fixed order, evaluates I, and writes the per-row and
+//              per-column score contributions; the CTA that merges the wave's
+//              last tile runs the wave finalisation (scores, threshold, prune,
+//              next wave or root).
+//   remove   rows of U spread over the CTAs: x_w <- (x_w - Sigma[w,root] x_root)
+//            / sqrt(1 - Sigma[w,root]^2) with the new H(x_w); then the covariance
+//            downdate of Eq. CovUpdate, in FP64.
+//
+// A wave pairs up to kTJ candidate variables (the columns) with every variable
+// that has not been a column yet in this iteration (the rows; the columns come
+// first among the rows so that pairs inside the block are covered).  Each
+// unordered pair is evaluated once and its measure I(i,j) of Eq. Itest serves
+// both variables (messaging, Sec. III-A: I(j,i) = -I(i,j)).  After the wave its
+// columns have met every other variable, so their scores (Algorithm 2) are
+// complete; the lowest complete score bounds the root's score (threshold,
+// Sec. III-B), and a variable whose partial score exceeds it can no longer be
+// the root and never becomes a column.  The iteration ends when no live
+// variable is left un-columned; the root is the complete variable of lowest
+// score (lowest index on ties).
+//
+// Per pair and sample the residuals are formed from the covariance rho =
+// Sigma[i,j] (Eq. var_update / Algorithm 7):
+//   a = (x_i - rho x_j)/sqrt(1-rho^2) = r_i^(j),  b = (x_j - rho x_i)/sqrt(1-rho^2) = r_j^(i),
+// and the two sample moments of Eq. HApp are accumulated for each:
+//   sum log cosh u  with  log cosh u = |u| + ln(1 + e^{-2|u|}) - ln 2,   and sum u e^{-u^2/2}.
+// The logarithm is taken once per group of kSub samples, of the product of the
+// factors 1 + e^{-2|u|}; in FP32 a sample costs two SFU base-2 exponentials per
+// residual.  Two consecutive samples travel together in packed f32x2
+// registers.  Group sums are centred (log cosh u - beta), keeping the FP32
+// running sums small.
+//
+// Compute work split: a wave is ntiles x (ld / CH) units (a TI x 32 pair tile
+// times a chunk of CH samples).  CTA b of the G working CTAs takes units
+// [b U / G, (b+1) U / G), contiguous and of equal length, and writes one
+// partial slot per tile it touches (slot index tile + b is unique).  Inside a
+// CTA the sample chunks of the TI + 32 variables of the current tile stream
+// into a shared-memory ring with 1-D bulk copies (TMA engine) completing on
+// mbarriers; the warp that releases a stage last refills it.  Every wait
+// (mbarrier phase, grid barrier) is bounded by the fit's timeout.
+#include <type_traits>
+
+#include "common.cuh"
+#include "launch.h"
+#include "tma.cuh"
+
+namespace lingam {
+
+// Tile geometry per precision: TI rows x kTJ columns, CONS threads of 2 x 2
+// pairs each (rows ty and ty + TI/2, columns tx and tx + 16), one CTA per SM.
+template <class T>
+struct PairCfg;
+template <>
+struct PairCfg<float> {
+    static constexpr int TI = 64;
+    static constexpr int CONS = 512;
+    static constexpr int CH = kChunk;
+    static constexpr int LDS = kChunk + 4;    // padded smem row: conflict-free 16-byte loads
+};
+template <>
+struct PairCfg<double> {
+    static constexpr int TI = 32;
+    static constexpr int CONS = 256;
+    static constexpr int CH = kChunk64;
+    static constexpr int LDS = kChunk64 + 2;  // padded smem row
+};
+
+constexpr int kSortMax = 8192;   // candidate sort in shared memory up to this many variables
+
+template <class T>
+__host__ __device__ constexpr size_t stage_elems() {
+    return size_t(PairCfg<T>::TI + kTJ) * PairCfg<T>::LDS;
+}
+template <class T>
+__host__ __device__ constexpr size_t ring_bytes() {
+    return size_t(kStages) * stage_elems<T>() * sizeof(T);
+}
+template <class T>
+size_t iter_smem_bytes() {
+    const size_t ring = ring_bytes<T>();
+    const size_t sort = size_t(kSortMax) * sizeof(unsigned long long);
+    return (ring > sort ? ring : sort) + kStages * sizeof(uint64_t);
+}
+
+// FP32 residuals carry the scale kScale: with u' = kScale*u,
+//   e^{-u^2/2} = 2^{-u'^2},   e^{-2|u|} = 2^{kC3 |u'|}.
+constexpr float kScale = 0.84932180028801904272f;     // sqrt(log2(e)/2)
+constexpr float kInvScale = 1.17741002251547469101f;  // 1/kScale
+constexpr float kC3 = -3.39728720115207617088f;       // -2 log2(e) / kScale
+
+// ------------------------------------------------------------------ small helpers
+// Values written by other CTAs during the same launch are read through L2 (the L1
+// caches of different SMs are not coherent).
+__device__ __forceinline__ int ld2(const int* p) { return __ldcg(p); }
+__device__ __forceinline__ double ld2(const double* p) { return __ldcg(p); }
+
+template <int NTH>
+__device__ __forceinline__ int scan01(int flag, int* red, int* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    const int pre = __popc(m & ((1u << lane) - 1u));
+    __syncthreads();
+    if (lane == 0) red[wid] = __popc(m);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < NTH / 32; ++w) {
+        off += (w < wid) ? red[w] : 0;
+        tot += red[w];
+    }
+    *total = tot;
+    return off + pre;
+}
+
+template <int NTH, class V>
+__device__ __forceinline__ V block_sum_n(V v, V* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    V s = V(0);
+    for (int w = 0; w < NTH / 32; ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+
+// 16 consecutive values (16-byte aligned) through L2.
+__device__ __forceinline__ void load16_cg(float* v, const float* src) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 x = __ldcg(reinterpret_cast<const float4*>(src) + k);
+        v[4 * k + 0] = x.x;
+        v[4 * k + 1] = x.y;
+        v[4 * k + 2] = x.z;
+        v[4 * k + 3] = x.w;
+    }
+}
+__device__ __forceinline__ void load16_cg(double* v, const double* src) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const double2 x = __ldcg(reinterpret_cast<const double2*>(src) + k);
+        v[2 * k + 0] = x.x;
+        v[2 * k + 1] = x.y;
+    }
+}
+
+// Grid-wide barrier (sense by generation count), bounded: returns false when this
+// CTA gave up (timeout, recorded) or another CTA did (ctl->abort).
+__device__ bool grid_sync(Ctl* ctl, unsigned long long tmo) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile int* genp = &ctl->bar_gen;
+        volatile int* abortp = &ctl->abort;
+        const int gen = *genp;
+        __threadfence();
+        if (atomicAdd(&ctl->bar_count, 1) == int(gridDim.x) - 1) {
+            ctl->bar_count = 0;
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*genp == gen) {
+                if (*abortp) {
+                    ok = 0;
+                    break;
+                }
+                if (global_ns() - t0 > tmo) {
+                    set_status(ctl, LINGAM_ETIMEOUT);
+                    ctl->abort = 1;
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok && !*abortp;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Bounded wait on an mbarrier phase that also gives up once the CTA (s_abort) or
+// the grid (ctl->abort) has given up.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, Ctl* ctl,
+                                                   unsigned long long tmo, volatile int* s_abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    volatile int* abortp = &ctl->abort;
+    for (;;) {
+        for (int k = 0; k < 64; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (*s_abort || *abortp) return false;
+        if (global_ns() - t0 > tmo) {
+            set_status(ctl, LINGAM_ETIMEOUT);
+            return false;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ unit ranges
+// Working CTAs of a wave with U units on a grid of Gmax: k = ceil(U / Gmax) units
+// per CTA at most, and the fewest CTAs that keep that bound, so that each tile is
+// shared by as few CTAs as possible (fewer partial slots to merge, same time).
+__device__ __forceinline__ long long working_ctas(long long U, long long Gmax) {
+    const long long k = (U + Gmax - 1) / Gmax;
+    return (U + k - 1) / k;
+}
+// CTA b of G owns units [lo(b), lo(b+1)), lo(b) = floor(b U / G).
+__device__ __forceinline__ long long unit_lo(long long b, long long U, long long G) { return b * U / G; }
+// The CTA whose range holds unit v: the smallest b with lo(b+1) > v.
+__device__ __forceinline__ int cta_of_unit(long long v, long long U, long long G) {
+    return int(((v + 1) * G + U - 1) / U) - 1;
+}
+
+// ------------------------------------------------------------------ plan (CTA 0)
+template <int NTH>
+__device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* smem, int* red) {
+    Ctl* ctl = f.ctl;
+    const int p = f.p, tid = threadIdx.x;
+    int r = 0;
+    for (int base = 0; base < p; base += NTH) {   // U in index order
+        const int v = base + tid;
+        const int a = (v < p) ? (f.flags[v] & kAlive) : 0;
+        int tot;
+        const int rank = r + scan01<NTH>(a ? 1 : 0, red, &tot);
+        if (a) f.sigma[rank] = v;
+        r += tot;
+        __syncthreads();
+    }
+    // Sort by key: the order-preserving bits of the float score above the variable
+    // index (ties by index).  Bitonic; compare-exchange stages with strides below 32
+    // run in registers.  Beyond kSortMax variables sigma stays in index order.
+    if (r <= kSortMax && r > 1) {
+        int N = 32;
+        while (N < r) N <<= 1;
+        unsigned long long* key = reinterpret_cast<unsigned long long*>(smem);
+        for (int k = tid; k < N; k += NTH) {
+            unsigned long long kv = ~0ull;
+            if (k < r) {
+                const int v = f.sigma[k];
+                const float sc = float(it == 0 ? f.hx[v] : f.prev[v]);
+                unsigned int bits = __float_as_uint(sc);
+                bits = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+                kv = (static_cast<unsigned long long>(bits) << 32) | static_cast<unsigned int>(v);
+            }
+            key[k] = kv;
+        }
+        __syncthreads();
+        for (int size = 2; size <= N; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                if (stride >= 32) {
+                    for (int k = tid; k < N; k += NTH) {
+                        const int l = k ^ stride;
+                        if (l > k) {
+                            const bool up = (k & size) == 0;
+                            const unsigned long long a = key[k], c = key[l];
+                            if ((a > c) == up) {
+                                key[k] = c;
+                                key[l] = a;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                } else {
+                    for (int k0 = 0; k0 < N; k0 += NTH) {
+                        const int k = k0 + tid;
+                        unsigned long long a = k < N ? key[k] : ~0ull;
+                        for (int st = stride; st > 0; st >>= 1) {
+                            const unsigned long long c = __shfl_xor_sync(0xffffffffu, a, st);
+                            const bool up = (k & size) == 0;
+                            const bool lower = (k & st) == 0;
+                            const unsigned long long lo = a < c ? a : c, hi = a < c ? c : a;
+                            a = (lower == up) ? lo : hi;
+                        }
+                        if (k < N) key[k] = a;
+                    }
+                    __syncthreads();
+                    break;
+                }
+            }
+        }
+        for (int k = tid; k < r; k += NTH) f.sigma[k] = int(key[k] & 0xffffffffu);
+        __syncthreads();
+        fence_proxy_async();   // this shared memory is the copy ring of later phases
+    }
+    for (int k = tid; k < r; k += NTH) {
+        const int v = f.sigma[k];
+        f.part[v] = 0.0;
+        f.flags[v] = kAlive;
+        f.rows[k] = v;
+    }
+    if (f.want_scores)
+        for (int v = tid; v < p; v += NTH) f.rep_scores[size_t(it) * p + v] = NAN;
+    __syncthreads();
+    if (tid == 0) {
+        ctl->it = it;
+        ctl->r = r;
+        ctl->wave = 0;
+        ctl->merged = 0;
+        ctl->best = INFINITY;
+        ctl->best_var = -1;
+        ctl->pairs_it = 0;
+        if (r <= 1) {
+            // Algorithm 2, lines 1-3: a single variable is the root
+            const int root = r == 1 ? f.sigma[0] : -1;
+            ctl->root = root;
+            ctl->done = 1;
+            if (root >= 0) {
+                f.order[it] = root;
+                if (f.want_scores) f.rep_scores[size_t(it) * p + root] = 0.0;
+            }
+            f.rep_root_score[it] = 0.0;
+            f.rep_margin[it] = INFINITY;
+            f.rep_pairs[it] = 0;
+            ctl->ncol = ctl->nrow = ctl->ntiles = 0;
+        } else {
+            ctl->done = 0;
+            const int nc = r < kTJ ? r : kTJ;
+            for (int c = 0; c < nc; ++c) f.cols[c] = f.sigma[c];
+            ctl->ncol = nc;
+            ctl->nrow = r;
+            const int ti = pair_tile_rows(f.precision);
+            ctl->ntiles = (r + ti - 1) / ti;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ wave finalisation
+// Run by one CTA (the one that merged the wave's last tile).
+template <int NTH, int TI>
+__device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
+    Ctl* ctl = f.ctl;
+    volatile Ctl* vc = ctl;
+    const int tid = threadIdx.x;
+    const int ncol = vc->ncol, nrow = vc->nrow, ntiles = vc->ntiles;
+    const int p = f.p, r = vc->r;
+
+    // 1. row contributions: min(0, I(row, col))^2 summed over the wave's columns
+    if (f.reuse)
+        for (int e = tid; e < nrow; e += NTH) {
+            const int v = ld2(f.rows + e);
+            f.part[v] = ld2(f.part + v) + ld2(f.rowsum + e);
+        }
+    __syncthreads();
+    // 2. column contributions max(0, I(row, col))^2 = min(0, I(col, row))^2 in tile order;
+    // 3. threshold = lowest complete score (lowest variable index on ties)
+    if (tid < 32) {
+        double sc = INFINITY;
+        int v = 0x7fffffff;
+        if (tid < ncol) {
+            double tot = 0.0;
+            for (int t = 0; t < ntiles; ++t) tot += ld2(f.colsum + t * kTJ + tid);
+            v = ld2(f.cols + tid);
+            sc = ld2(f.part + v) + tot;
+            f.part[v] = sc;
+            f.flags[v] = ld2(f.flags + v) | kColumned;
+            if (f.want_scores) f.rep_scores[(size_t)it * p + v] = sc;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double so = __shfl_xor_sync(0xffffffffu, sc, o);
+            const int vo = __shfl_xor_sync(0xffffffffu, v, o);
+            if (so < sc || (so == sc && vo < v)) {
+                sc = so;
+                v = vo;
+            }
+        }
+        if (tid == 0) {
+            const double best = vc->best;
+            const int bv = vc->best_var;
+            if (bv < 0 || sc < best || (sc == best && v < bv)) {
+                ctl->best = sc;
+                ctl->best_var = v;
+            }
+            ctl->pairs_it += f.reuse ? (long long)ncol * (ncol - 1) / 2 + (long long)ncol * (nrow - ncol)
+                                     : (long long)ncol * (nrow - 1);
+        }
+    }
+    __syncthreads();
+    const double best = vc->best;
+
+    // 4. prune, then pick the next columns: the first kTJ live un-columned variables
+    //    in candidate order.
+    int nc = 0;
+    for (int base = 0; base < r; base += NTH) {
+        const int k = base + tid;
+        int live = 0, v = -1;
+        if (k < r) {
+            v = ld2(f.sigma + k);
+            int fl = ld2(f.flags + v);
+            if (!(fl & kColumned)) {
+                if (!(fl & kDead) && f.prune && f.reuse && ld2(f.part + v) > best) {
+                    fl |= kDead;
+                    f.flags[v] = fl;
+                }
+                live = (fl & kDead) ? 0 : 1;
+            }
+        }
+        int tot;
+        const int rank = nc + scan01<NTH>(live, red, &tot);
+        if (live && rank < kTJ) {
+            f.cols[rank] = v;
+            f.flags[v] = ld2(f.flags + v) | kPick;
+        }
+        nc += tot;
+        __syncthreads();
+    }
+    nc = nc < kTJ ? nc : kTJ;
+    __syncthreads();
+    // 5. rows of the next wave: the columns, then every other row-eligible variable
+    //    (un-columned ones with reuse; all remaining ones without) in candidate order.
+    int nr = 0;
+    for (int base = 0; base < r; base += NTH) {
+        const int k = base + tid;
+        int take = 0, v = -1;
+        if (k < r) {
+            v = ld2(f.sigma + k);
+            const int fl = ld2(f.flags + v);
+            take = !(fl & kPick) && (!f.reuse || !(fl & kColumned));
+        }
+        int tot;
+        const int rank = nr + scan01<NTH>(take, red, &tot);
+        if (take) f.scratch[rank] = v;
+        nr += tot;
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int k = tid; k < nc + nr; k += NTH) f.rows[k] = k < nc ? ld2(f.cols + k) : ld2(f.scratch + k - nc);
+    for (int c = tid; c < nc; c += NTH) {
+        const int v = ld2(f.cols + c);
+        f.flags[v] = ld2(f.flags + v) & ~kPick;
+    }
+    __syncthreads();
+
+    // 6. no live variable left: the root is the complete variable of lowest score (or
+    //    the forced one); the margin bound is the lowest other score (full if complete,
+    //    else a lower bound) minus the root's.
+    double second = INFINITY;
+    if (nc == 0) {
+        __shared__ double s_min[32];
+        const int bv = vc->best_var;
+        for (int k = tid; k < r; k += NTH) {
+            const int v = ld2(f.sigma + k);
+            if (v != bv) second = fmin(second, ld2(f.part + v));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) second = fmin(second, __shfl_xor_sync(0xffffffffu, second, o));
+        if ((tid & 31) == 0) s_min[tid >> 5] = second;
+        __syncthreads();
+        if (tid == 0)
+            for (int w = 0; w < NTH / 32; ++w) second = fmin(second, s_min[w]);
+    }
+    if (tid == 0) {
+        if (nc == 0) {
+            const int root = f.has_forced ? f.forced[it] : vc->best_var;
+            ctl->root = root;
+            ctl->done = 1;
+            f.order[it] = root;
+            f.rep_root_score[it] = ld2(f.part + root);
+            f.rep_margin[it] = second - vc->best;
+            f.rep_pairs[it] = vc->pairs_it;
+        } else {
+            ctl->ncol = nc;
+            ctl->nrow = nc + nr;
+            ctl->ntiles = (nc + nr + TI - 1) / TI;
+            ctl->wave += 1;
+        }
+        ctl->merged = 0;
+    }
+}
+
+// ------------------------------------------------------------------ per-sample math (FP32)
+// Two consecutive samples of one residual u' (scaled by kScale).
+struct Acc2 {
+    float2 A, P, G;   // sum of kC3 |u'|, product of (1 + e^{-2|u|}), sum of u' e^{-u^2/2}; per half
+};
+__device__ __forceinline__ void acc2_add(Acc2& s, float2 u) {
+    const float2 q = __fmul2_rn(u, u);
+    float2 g;
+    g.x = ex2_approx(-q.x);
+    g.y = ex2_approx(-q.y);
+    s.G = __ffma2_rn(u, g, s.G);
+    float2 t;
+    t.x = fabsf(u.x) * kC3;
+    t.y = fabsf(u.y) * kC3;
+    float2 e;
+    e.x = ex2_approx(t.x);
+    e.y = ex2_approx(t.y);
+    s.P = __ffma2_rn(s.P, e, s.P);
+    s.A = __fadd2_rn(s.A, t);
+}
+
+// ------------------------------------------------------------------ copy ring
+// Warp-cooperative: lane 0 posts the expected bytes, the lanes issue one 1-D bulk
+// copy per variable of the tile (rows then columns) for one chunk of samples.
+template <class T>
+__device__ __forceinline__ void issue_chunk(const Fit& f, T* stage, uint64_t* bar, long long unit, int nch, int nrow,
+                                            int ncol) {
+    using Cfg = PairCfg<T>;
+    constexpr int CH = Cfg::CH, LDS = Cfg::LDS, TI = Cfg::TI;
+    constexpr int SLOTS = (TI + kTJ + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const int t = int(unit / nch), c = int(unit % nch);
+    const T* xt = static_cast<const T*>(f.xt);
+    const size_t t0 = size_t(c) * CH;
+    int vars[SLOTS];
+    int nvalid = 0;
+#pragma unroll
+    for (int k = 0; k < SLOTS; ++k) {
+        const int slot = lane + 32 * k;
+        int v = -1;
+        if (slot < TI) {
+            const int row = t * TI + slot;
+            v = row < nrow ? ld2(f.rows + row) : -1;
+        } else if (slot < TI + kTJ) {
+            v = (slot - TI) < ncol ? ld2(f.cols + slot - TI) : -1;
+        }
+        vars[k] = v;
+        nvalid += __popc(__ballot_sync(0xffffffffu, v >= 0));
+    }
+    if (lane == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(bar, uint32_t(nvalid) * CH * sizeof(T));
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < SLOTS; ++k) {
+        const int slot = lane + 32 * k;
+        if (vars[k] >= 0) bulk_g2s(stage + slot * LDS, xt + size_t(vars[k]) * f.ld + t0, CH * sizeof(T), bar);
+    }
+}
+
+// Shared state of one CTA (besides the dynamic copy ring).
+template <class T>
+struct IterShared {
+    int red[32];
+    int arrive[kStages];
+    int issued;
+    int abort;
+    int flag;
+    double dred[32];
+};
+
+// ------------------------------------------------------------------ compute phase
+// Returns false when a wait gave up (the CTA then leaves the kernel).
+struct Wave {
+    int ntiles, ncol, nrow;
+};
+
+template <class T>
+__device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring, uint64_t* full, IterShared<T>& sh,
+                              int& chunk_base) {
+    using Cfg = PairCfg<T>;
+    constexpr int CH = Cfg::CH, LDS = Cfg::LDS, TI = Cfg::TI, CONS = Cfg::CONS;
+    constexpr int NW = CONS / 32;
+    constexpr bool kF32 = std::is_same<T, float>::value;
+    Ctl* ctl = f.ctl;
+    const int ntiles = wv.ntiles, ncol = wv.ncol, nrow = wv.nrow;
+    const int p = f.p;
+    const int nch = f.ld / CH;
+    const long long U = (long long)ntiles * nch, G = working_ctas(U, gridDim.x);
+    const int b = blockIdx.x;
+    if (b >= G) return true;   // no unit for this CTA in this wave
+    const long long u_lo = unit_lo(b, U, G), u_hi = unit_lo(b + 1, U, G);
+    const int total = int(u_hi - u_lo);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned long long tmo = ctl->timeout_ns;
+    const int base = chunk_base;   // ring position of this wave's first chunk
+
+    if (tid < 32)
+        for (int k = 0; k < min(total, kStages); ++k) {
+            const int s = (base + k) % kStages;
+            issue_chunk<T>(f, ring + size_t(s) * stage_elems<T>(), &full[s], u_lo + k, nch, nrow, ncol);
+        }
+    if (tid == 0) sh.issued = min(total, kStages);
+
+    const int ty = tid >> 4, tx = tid & 15;
+    const int rsl[2] = {ty, ty + TI / 2}, csl[2] = {tx, tx + 16};
+    const T grp_off = T(-double(kSub) * (kLn2 + kBeta));
+    T* parts = static_cast<T*>(f.partials);
+    int k = 0;   // chunk index within this wave (this CTA)
+    bool ok = true;
+    for (long long u = u_lo; u < u_hi;) {
+        const int t = int(u / nch), c0 = int(u % nch);
+        const int c1 = int(min((long long)nch, c0 + (u_hi - u)));
+        T s_[4], sr_[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = t * TI + rsl[q >> 1], c = csl[q & 1];
+            const int vi = e < nrow ? ld2(f.rows + e) : -1;
+            const int vj = c < ncol ? ld2(f.cols + c) : -1;
+            bool okp = vi >= 0 && vj >= 0;
+            if (okp) okp = f.reuse ? (e >= ncol || c < e) : (vi != vj);
+            double rho = okp ? f.sig[size_t(vi) * p + vj] : 0.0;
+            double om = fma(-rho, rho, 1.0);   // 1 - rho^2 in FP64
+            if (okp && !(om > 1e-14)) {
+                set_status(ctl, LINGAM_EDEGENERATE);
+                om = 1.0;
+                rho = 0.0;
+            }
+            if constexpr (kF32) {
+                const float sc = kScale / sqrtf(float(om));
+                s_[q] = sc;
+                sr_[q] = sc * float(rho);
+            } else {
+                const double sc = 1.0 / sqrt(om);
+                s_[q] = sc;
+                sr_[q] = sc * rho;
+            }
+        }
+        // D = sum over closed groups of (log cosh u - beta), Gt = sum of u e^{-u^2/2}
+        T D[8], Gt[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            D[j] = T(0);
+            Gt[j] = T(0);
+        }
+        for (int c = c0; c < c1; ++c, ++k) {
+            const int pos = base + k;
+            const int s = pos % kStages;
+            if (!mbar_wait_or_abort(&full[s], (pos / kStages) & 1, ctl, tmo, &sh.abort)) {
+                ok = false;
+                sh.abort = 1;
+                break;
+            }
+            const T* st = ring + size_t(s) * stage_elems<T>();
+            const T* R0 = st + rsl[0] * LDS;
+            const T* R1 = st + rsl[1] * LDS;
+            const T* C0 = st + (TI + csl[0]) * LDS;
+            const T* C1 = st + (TI + csl[1]) * LDS;
+            if constexpr (kF32) {
+                float2 s2[4], sr2[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    s2[q] = make_float2(s_[q], s_[q]);
+                    sr2[q] = make_float2(-sr_[q], -sr_[q]);
+                }
+#pragma unroll 1
+                for (int tt = 0; tt < CH; tt += kSub) {
+                    Acc2 acc[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        acc[j].A = make_float2(0.f, 0.f);
+                        acc[j].P = make_float2(1.f, 1.f);
+                        acc[j].G = make_float2(0.f, 0.f);
+                    }
+#pragma unroll 2
+                    for (int uu = 0; uu < kSub; uu += 4) {
+                        const float4 xr0 = *reinterpret_cast<const float4*>(R0 + tt + uu);
+                        const float4 xr1 = *reinterpret_cast<const float4*>(R1 + tt + uu);
+                        const float4 xc0 = *reinterpret_cast<const float4*>(C0 + tt + uu);
+                        const float4 xc1 = *reinterpret_cast<const float4*>(C1 + tt + uu);
+                        const float2 xi[2][2] = {{make_float2(xr0.x, xr0.y), make_float2(xr0.z, xr0.w)},
+                                                 {make_float2(xr1.x, xr1.y), make_float2(xr1.z, xr1.w)}};
+                        const float2 xj[2][2] = {{make_float2(xc0.x, xc0.y), make_float2(xc0.z, xc0.w)},
+                                                 {make_float2(xc1.x, xc1.y), make_float2(xc1.z, xc1.w)}};
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const float2 vi = xi[q >> 1][h], vj = xj[q & 1][h];
+                                const float2 a = __ffma2_rn(s2[q], vi, __fmul2_rn(sr2[q], vj));
+                                const float2 bb = __ffma2_rn(s2[q], vj, __fmul2_rn(sr2[q], vi));
+                                acc2_add(acc[2 * q], a);
+                                acc2_add(acc[2 * q + 1], bb);
+                            }
+                        }
+                    }
+                    // close the group: one lg2 per residual for both halves' products;
+                    // sum |u| = (sum kC3 |u'|) / (kC3 kScale)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float lsum = lg2_approx(acc[j].P.x * acc[j].P.y);
+                        const float asum = acc[j].A.x + acc[j].A.y;
+                        D[j] += fmaf(float(kLn2), lsum, fmaf(asum, kInvScale / kC3, grp_off));
+                        Gt[j] += acc[j].G.x + acc[j].G.y;
+                    }
+                }
+            } else {
+#pragma unroll 1
+                for (int tt = 0; tt < CH; tt += kSub) {
+                    T A[8], P[8], Gs[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        A[j] = T(0);
+                        P[j] = T(1);
+                        Gs[j] = T(0);
+                    }
+#pragma unroll 1
+                    for (int uu = 0; uu < kSub; ++uu) {
+                        const double xi[2] = {R0[tt + uu], R1[tt + uu]};
+                        const double xj[2] = {C0[tt + uu], C1[tt + uu]};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const double a = fma(s_[q], xi[q >> 1], -sr_[q] * xj[q & 1]);
+                            const double bb = fma(s_[q], xj[q & 1], -sr_[q] * xi[q >> 1]);
+                            const double aa = fabs(a), ab = fabs(bb);
+                            P[2 * q] = fma(P[2 * q], exp(-2.0 * aa), P[2 * q]);
+                            P[2 * q + 1] = fma(P[2 * q + 1], exp(-2.0 * ab), P[2 * q + 1]);
+                            A[2 * q] += aa;
+                            A[2 * q + 1] += ab;
+                            Gs[2 * q] = fma(a, exp(-0.5 * a * a), Gs[2 * q]);
+                            Gs[2 * q + 1] = fma(bb, exp(-0.5 * bb * bb), Gs[2 * q + 1]);
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        D[j] += A[j] + log(P[j]) + grp_off;
+                        Gt[j] += Gs[j];
+                    }
+                }
+            }
+            // release the stage; the last warp to release it refills it with the chunk
+            // kStages further on
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) {
+                __threadfence_block();
+                last = atomicAdd(&sh.arrive[s], 1) == NW - 1;
+                if (last) {
+                    sh.arrive[s] = 0;
+                    __threadfence_block();
+                }
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last && k + kStages < total) {
+                const int s2i = (pos + kStages) % kStages;
+                issue_chunk<T>(f, ring + size_t(s2i) * stage_elems<T>(), &full[s2i], u_lo + k + kStages, nch, nrow,
+                               ncol);
+                if (lane == 0) atomicMax(&sh.issued, k + kStages + 1);
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            // A wait gave up (status recorded).  Give the copies still in flight a bounded
+            // chance to land before the CTA leaves.
+            if (tid == 0)
+                for (int k2 = k; k2 < sh.issued; ++k2) {
+                    const int pos = base + k2;
+                    const unsigned long long t0 = global_ns();
+                    while (!mbar_try_wait(&full[pos % kStages], (pos / kStages) & 1) &&
+                           global_ns() - t0 < 2000000000ull) {
+                    }
+                }
+            __syncthreads();
+            return false;
+        }
+        // this CTA's partial moments of tile t: slot t + b
+        T* dst = parts + ((size_t(t) + b) * CONS + tid) * 16;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            dst[4 * q + 0] = D[2 * q];
+            dst[4 * q + 1] = Gt[2 * q];
+            dst[4 * q + 2] = D[2 * q + 1];
+            dst[4 * q + 3] = Gt[2 * q + 1];
+        }
+        u += c1 - c0;
+    }
+    chunk_base = base + total;
+    return true;
+}
+
+// ------------------------------------------------------------------ merge phase
+// A tile's partial slots are merged in kMergeParts items, one per group of 64
+// compute threads (256 pairs, 1024 values per slot), spread over the CTAs.  In an
+// item each warp sums the slots w, w + NW, ... in order, then the warps' sums are
+// added in warp order: a fixed summation order, independent of timing.  The item
+// evaluates I (Eq. Itest with Eq. HApp) for its 256 pairs and stores them in the
+// tile's I buffer; the item that completes a tile reduces its rows and columns
+// (squared contributions summed in FP64), and the item that completes the wave's
+// last tile runs the wave finalisation.
+template <class T>
+__device__ __noinline__ void merge_phase(const Fit& f, const Wave& wv, int it, IterShared<T>& sh, T* scratch) {
+    using Cfg = PairCfg<T>;
+    constexpr int CH = Cfg::CH, TI = Cfg::TI, CONS = Cfg::CONS;
+    constexpr int NW = CONS / 32;
+    constexpr int PARTS = CONS / 64;            // items per tile
+    constexpr bool kF32 = std::is_same<T, float>::value;
+    Ctl* ctl = f.ctl;
+    const int ntiles = wv.ntiles, ncol = wv.ncol, nrow = wv.nrow;
+    const int ld = f.ld, nch = ld / CH;
+    const long long U = (long long)ntiles * nch, G = working_ctas(U, gridDim.x);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const T* parts = static_cast<const T*>(f.partials);
+    T* ibuf = static_cast<T*>(f.ibuf);
+    const double n = double(f.n);
+    const double pad_fix = double(ld - f.n) * kBeta;   // each zero padding sample added -beta
+    const int nitems = ntiles * PARTS;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int t = item / PARTS, part = item % PARTS;
+        const int b_first = cta_of_unit((long long)t * nch, U, G);
+        const int b_last = cta_of_unit((long long)(t + 1) * nch - 1, U, G);
+        // 1. per warp: slots b_first + wid, + NW, ...; each lane 32 of the item's 1024 values
+        T acc[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc[k] = T(0);
+        for (int bb = b_first + wid; bb <= b_last; bb += NW) {
+            const T* src = parts + ((size_t(t) + bb) * CONS + part * 64) * 16 + lane * 32;
+            T v[32];
+            load16_cg(v, src);
+            load16_cg(v + 16, src + 16);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) acc[k] += v[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 32; ++k) scratch[wid * 1024 + lane * 32 + k] = acc[k];
+        __syncthreads();
+        // 2. one thread per pair: warps' sums in warp order, then I
+        if (tid < 256) {
+            T tot[4] = {T(0), T(0), T(0), T(0)};
+            for (int w = 0; w < NW; ++w)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) tot[k] += scratch[w * 1024 + tid * 4 + k];
+            // pair tid of the item = pair (tid & 3) of compute thread part * 64 + tid / 4
+            const int ct = part * 64 + (tid >> 2), q = tid & 3;
+            const int e_loc = (ct >> 4) + (q >> 1) * (TI / 2), cc = (ct & 15) + (q & 1) * 16;
+            const int e = t * TI + e_loc;
+            const int vi = e < nrow ? ld2(f.rows + e) : -1;
+            const int vj = cc < ncol ? ld2(f.cols + cc) : -1;
+            bool okp = vi >= 0 && vj >= 0;
+            if (okp) okp = f.reuse ? (e >= ncol || cc < e) : (vi != vj);
+            T I = T(0);
+            if (okp) {
+                if constexpr (kF32) {
+                    const float inv_n = float(1.0 / n);
+                    const float ha = hterm_f(tot[0] + float(pad_fix), tot[1] * kInvScale, inv_n);
+                    const float hb = hterm_f(tot[2] + float(pad_fix), tot[3] * kInvScale, inv_n);
+                    I = (float(f.hx[vj]) - float(f.hx[vi])) + (ha - hb);
+                } else {
+                    const double ha = hterm(tot[0] + pad_fix, tot[1], n);
+                    const double hb = hterm(tot[2] + pad_fix, tot[3], n);
+                    I = (f.hx[vj] - f.hx[vi]) + (ha - hb);
+                }
+                if (!isfinite(double(I))) set_status(ctl, LINGAM_EDEGENERATE);
+            }
+            ibuf[(size_t(t) * TI + e_loc) * kTJ + cc] = I;
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) sh.flag = (atomicAdd(f.tile_cnt + t, 1) == PARTS - 1);
+        __syncthreads();
+        if (sh.flag) {
+            // 3. the tile's last item: per-row and per-column contributions in FP64
+            __threadfence();
+            const T* It = ibuf + size_t(t) * TI * kTJ;
+            if (tid < TI) {
+                const int e = t * TI + tid;
+                double s = 0.0;
+                for (int cc = 0; cc < kTJ; ++cc) {
+                    const double I = double(__ldcg(It + tid * kTJ + cc));
+                    const double m = I < 0.0 ? I : 0.0;
+                    s = fma(m, m, s);
+                }
+                if (e < nrow) f.rowsum[e] = s;
+            } else if (tid < TI + kTJ) {
+                const int cc = tid - TI;
+                double s = 0.0;
+                for (int e = 0; e < TI; ++e) {
+                    const double I = double(__ldcg(It + e * kTJ + cc));
+                    const double m = I > 0.0 ? I : 0.0;
+                    s = fma(m, m, s);
+                }
+                f.colsum[t * kTJ + cc] = s;
+            }
+            if (tid == 0) f.tile_cnt[t] = 0;
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) sh.flag = (atomicAdd(&ctl->merged, 1) == ntiles - 1);
+            __syncthreads();
+            if (sh.flag) {
+                __threadfence();
+                wave_finalize<CONS, TI>(f, it, sh.red);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ removal phases
+// UpdateData (Algorithm 7) with the new H(x_w) terms; rows of U spread over the CTAs.
+template <class T>
+__device__ __noinline__ void remove_data_phase(const Fit& f, IterShared<T>& sh) {
+    constexpr int NTH = PairCfg<T>::CONS;
+    Ctl* ctl = f.ctl;
+    volatile Ctl* vc = ctl;
+    const int r = vc->r, root = vc->root, p = f.p, ld = f.ld, tid = threadIdx.x;
+    for (int k = blockIdx.x; k < r; k += gridDim.x) {
+        const int w = ld2(f.sigma + k);
+        if (tid == 0) f.prev[w] = ld2(f.part + w);
+        if (w == root) {
+            if (tid == 0) {
+                f.flags[w] = 0;
+                f.inv_root[w] = 0.0;
+            }
+            continue;
+        }
+        const double c = f.sig[size_t(w) * p + root];
+        double om = fma(-c, c, 1.0);
+        if (!(om > 1e-14)) {
+            if (tid == 0) set_status(ctl, LINGAM_EDEGENERATE);
+            om = 1.0;
+        }
+        const double inv = 1.0 / sqrt(om);
+        if (tid == 0) f.inv_root[w] = inv;
+        T* xw = static_cast<T*>(f.xt) + size_t(w) * ld;
+        const T* xr = static_cast<const T*>(f.xt) + size_t(root) * ld;
+        T lcc = T(0), g = T(0);
+        if constexpr (std::is_same<T, float>::value) {
+            const float cc = float(c), ii = float(inv);
+            float4* xw4 = reinterpret_cast<float4*>(xw);
+            const float4* xr4 = reinterpret_cast<const float4*>(xr);
+            for (int t4 = tid; t4 < ld / 4; t4 += NTH) {
+                const float4 a = xw4[t4], rr = xr4[t4];
+                float4 o;
+                o.x = fmaf(-cc, rr.x, a.x) * ii;
+                o.y = fmaf(-cc, rr.y, a.y) * ii;
+                o.z = fmaf(-cc, rr.z, a.z) * ii;
+                o.w = fmaf(-cc, rr.w, a.w) * ii;
+                xw4[t4] = o;   // padding samples stay exactly zero
+                const int t = 4 * t4;
+                if (t + 0 < f.n) mom_add(o.x, lcc, g);
+                if (t + 1 < f.n) mom_add(o.y, lcc, g);
+                if (t + 2 < f.n) mom_add(o.z, lcc, g);
+                if (t + 3 < f.n) mom_add(o.w, lcc, g);
+            }
+        } else {
+            for (int t = tid; t < ld; t += NTH) {
+                const double u = fma(-c, xr[t], xw[t]) * inv;
+                xw[t] = u;
+                if (t < f.n) mom_add(u, lcc, g);
+            }
+        }
+        const double L = block_sum_n<NTH>(double(lcc), sh.dred);
+        const double Gs = block_sum_n<NTH>(double(g), sh.dred);
+        if (tid == 0) f.hx[w] = hterm(L, Gs, double(f.n));
+    }
+}
+
+// UpdateCovMat (Algorithm 8 / Eq. CovUpdate) on the normalised rows, in FP64, for
+// w, j in U without the root; rows spread over the CTAs, columns in index order.
+// Sigma is symmetric, so Sigma[j,root] is read from the root's row (contiguous).
+// The root's row and column are only read, so the update is done in place.
+template <class T>
+__device__ __noinline__ void remove_cov_phase(const Fit& f) {
+    constexpr int NTH = PairCfg<T>::CONS;
+    volatile Ctl* vc = f.ctl;
+    const int r = vc->r, root = vc->root, p = f.p, tid = threadIdx.x;
+    const double* rootrow = f.sig + size_t(root) * p;
+    for (int a = blockIdx.x; a < r; a += gridDim.x) {
+        const int w = ld2(f.sigma + a);
+        if (w == root) continue;
+        const double cw = rootrow[w], iw = ld2(f.inv_root + w);
+        double* row = f.sig + size_t(w) * p;
+        for (int j = tid; j < p; j += NTH) {
+            if (j == root || !(ld2(f.flags + j) & kAlive)) continue;
+            if (j == w) row[j] = 1.0;
+            else row[j] = (row[j] - cw * rootrow[j]) * (iw * ld2(f.inv_root + j));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ the iteration kernel
+template <class T>
+__global__ void __launch_bounds__(PairCfg<T>::CONS, 1) k_iteration(Fit f, int it) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ IterShared<T> sh;
+    using Cfg = PairCfg<T>;
+    Ctl* ctl = f.ctl;
+    T* ring = reinterpret_cast<T*>(smem_raw);
+    const size_t ring_or_sort = ring_bytes<T>() > size_t(kSortMax) * 8 ? ring_bytes<T>() : size_t(kSortMax) * 8;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + ring_or_sort);
+    volatile Ctl* vc = ctl;
+    // A failure recorded before this launch: every CTA reads it before the first
+    // barrier, so all of them leave together.
+    if (vc->status != 0) return;
+    const unsigned long long tmo = vc->timeout_ns;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            sh.arrive[s] = 0;
+        }
+        sh.abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (blockIdx.x == 0) plan_phase<Cfg::CONS>(f, it, smem_raw, sh.red);
+    if (!grid_sync(ctl, tmo)) return;
+    int chunk_base = 0;
+    while (!vc->done) {
+        const Wave wv = {vc->ntiles, vc->ncol, vc->nrow};
+        if (!compute_phase<T>(f, wv, ring, full, sh, chunk_base)) {
+            ctl->abort = 1;
+            return;
+        }
+        if (!grid_sync(ctl, tmo)) return;
+        merge_phase<T>(f, wv, it, sh, ring);
+        fence_proxy_async();   // the merge used the copy ring as scratch
+        if (!grid_sync(ctl, tmo)) return;
+    }
+    if (it < f.p - 1 && vc->root >= 0) {
+        remove_data_phase<T>(f, sh);
+        if (!grid_sync(ctl, tmo)) return;
+        remove_cov_phase<T>(f);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+template <class T>
+static int grid_for(int nsm) {
+    int per_sm = 0;
+    const size_t smem = iter_smem_bytes<T>();
+    if (ensure_smem_attr(reinterpret_cast<const void*>(k_iteration<T>), smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iteration<T>, PairCfg<T>::CONS, smem) !=
+        cudaSuccess)
+        return 0;
+    return per_sm >= 1 ? nsm : 0;   // one CTA per SM
+}
+
+int iteration_grid(const Fit& f, int nsm) {
+    return f.precision == LINGAM_MIXED ? grid_for<float>(nsm) : grid_for<double>(nsm);
+}
+
+template <class T>
+static cudaError_t launch_iter(const Fit& f, int it, int grid, cudaStream_t st) {
+    const size_t smem = iter_smem_bytes<T>();
+    cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(k_iteration<T>), smem);
+    if (e != cudaSuccess) return e;
+    Fit fc = f;
+    void* args[] = {&fc, &it};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_iteration<T>), dim3(grid),
+                                       dim3(PairCfg<T>::CONS), args, smem, st);
+}
+
+cudaError_t launch_iteration(const Fit& f, int it, int grid, cudaStream_t st) {
+    return f.precision == LINGAM_MIXED ? launch_iter<float>(f, it, grid, st) : launch_iter<double>(f, it, grid, st);
+}
+
+}  // namespace lingam

@@ -16,12 +16,11 @@ cudaError_t ensure_smem_attr(const void* func, size_t bytes);
 cudaError_t launch_standardize(const Fit& f, const void* x, int input_dtype, cudaStream_t st);
 // Sigma = Xn Xn^T / (n-1) of the normalised rows (Alg. 3 line 4); sig0 = sig.
 cudaError_t launch_gram(const Fit& f, cudaStream_t st);
-// Start of iteration `it`: candidate order, score reset, first wave.
-cudaError_t launch_plan(const Fit& f, int it, int nsplit, cudaStream_t st);
-// One wave of pair comparisons (and, in its last CTA, the wave finalisation).
-cudaError_t launch_pair_wave(const Fit& f, int it, int grid, cudaStream_t st);
-// Remove the root from the data (Alg. 7) and from the covariance (Alg. 8).
-cudaError_t launch_remove_root(const Fit& f, int it, int r, cudaStream_t st);
+// One iteration of Algorithm 3 (ParaFindRoot, UpdateData, UpdateCovMat) as one
+// persistent cooperative launch; grid = SMs.
+cudaError_t launch_iteration(const Fit& f, int it, int grid, cudaStream_t st);
+// Largest co-resident grid of the iteration kernel (one CTA per SM).
+int iteration_grid(const Fit& f, int nsm);
 // B from the order: Cholesky of the covariance in causal order, B = I - diag(R) R^{-1}.
 cudaError_t launch_fit_B(const Fit& f, cudaStream_t st);
 

@@ -33,6 +33,7 @@ cudaError_t ensure_smem_attr(const void* func, size_t bytes) {
 }
 
 constexpr long long kMaxP = 16384;
+constexpr int kMaxGrid = 1024;   // pair-kernel CTAs at most (2 per SM)
 constexpr size_t kAlign = 256;
 
 static size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -41,7 +42,7 @@ struct Layout {
     size_t total = 0;
     size_t off_xin, off_xt, off_mu, off_sd, off_sig, off_sig0, off_hx, off_part, off_prev, off_flags, off_sigma,
         off_rows, off_cols, off_order, off_forced, off_scratch, off_rowsum, off_colsum, off_partials, off_invroot,
-        off_tilecnt, off_rs, off_rm, off_rp, off_rsc, off_cmat, off_rmat, off_rinv, off_bout, off_ctl;
+        off_tilecnt, off_rs, off_rm, off_rp, off_rsc, off_cmat, off_rmat, off_rinv, off_bout, off_ctl, off_ibuf;
     int ld, maxtiles, maxsplit, esz;
 };
 
@@ -80,9 +81,13 @@ static Layout make_layout(long long p, long long n, int precision, int input_dty
     L.off_scratch = take(P * 4);
     L.off_rowsum = take(P * 8);
     L.off_colsum = take(size_t(L.maxtiles) * kTJ * 8);
-    L.off_partials = take(size_t(L.maxtiles) * L.maxsplit * kPairThreads * 16 * L.esz);
+    // one partial-moment slot per (tile, CTA) segment; slot index tile + CTA, and a wave never
+    // uses more CTAs than it has (tile, chunk) units
+    const size_t units = size_t(L.maxtiles) * size_t(L.ld / chunk_of(precision));
+    L.off_partials = take((size_t(L.maxtiles) + std::min(size_t(kMaxGrid), units)) * kPairThreads * 16 * L.esz);
     L.off_invroot = take(P * 8);
     L.off_tilecnt = take(size_t(L.maxtiles) * 4);
+    L.off_ibuf = take(size_t(L.maxtiles) * 64 * kTJ * L.esz);
     L.off_rs = take(P * 8);
     L.off_rm = take(P * 8);
     L.off_rp = take(P * 8);
@@ -108,17 +113,6 @@ static bool is_device_ptr(const void* ptr) {
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-// Sample-axis split of the pair kernel: enough CTAs for two per SM on the
-// first wave of the iteration, each split at least one chunk long.
-static int choose_split(int r, int ld, int precision, int nsm, int override_split, int maxsplit) {
-    if (override_split > 0) return std::min(override_split, maxsplit);
-    const int tiles = (r + kTI - 1) / kTI;
-    const int target = 2 * nsm;
-    int s = (target + tiles - 1) / tiles;
-    s = std::min(s, ld / chunk_of(precision));
-    return std::max(1, std::min(s, maxsplit));
 }
 
 static int fit_one(const void* X, long long p_, long long n_, int* order, double* B, void* workspace,
@@ -173,6 +167,7 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
     f.partials = base + L.off_partials;
     f.inv_root = reinterpret_cast<double*>(base + L.off_invroot);
     f.tile_cnt = reinterpret_cast<int*>(base + L.off_tilecnt);
+    f.ibuf = base + L.off_ibuf;
     f.rep_root_score = reinterpret_cast<double*>(base + L.off_rs);
     f.rep_margin = reinterpret_cast<double*>(base + L.off_rm);
     f.rep_pairs = reinterpret_cast<long long*>(base + L.off_rp);
@@ -228,33 +223,25 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
         if (launch_gram(f, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
         if (cudaEventRecord(ev[2], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
         launches += 2;
+        const int grid = iteration_grid(f, nsm);
+        if (grid < 1) {
+            status = LINGAM_ECUDA;
+            break;
+        }
         for (int it = 0; it < iters && status == LINGAM_OK; ++it) {
-            const int r = p - it;
-            const int S = choose_split(r, L.ld, o.precision, nsm, o.split_n, L.maxsplit);
-            if (launch_plan(f, it, S, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
-            ++launches;
-            if (r >= 2) {
-                const int waves = (r + kTJ - 1) / kTJ;
-                const int grid = ((r + kTI - 1) / kTI) * S;
-                cudaEvent_t e0 = nullptr, e1 = nullptr;
-                if (o.timing) {
-                    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-                        status = LINGAM_ECUDA;
-                        break;
-                    }
-                    pev.push_back(e0);
-                    pev.push_back(e1);
-                    cudaEventRecord(e0, st);
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (o.timing) {
+                if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+                    status = LINGAM_ECUDA;
+                    break;
                 }
-                for (int w = 0; w < waves; ++w)
-                    if (launch_pair_wave(f, it, grid, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
-                launches += waves;
-                if (o.timing) cudaEventRecord(e1, st);
+                pev.push_back(e0);
+                pev.push_back(e1);
+                cudaEventRecord(e0, st);
             }
-            if (status == LINGAM_OK && it < p - 1) {
-                if (launch_remove_root(f, it, r, st) != cudaSuccess) status = LINGAM_ECUDA;
-                launches += 2;
-            }
+            if (launch_iteration(f, it, grid, st) != cudaSuccess) status = LINGAM_ECUDA;
+            ++launches;
+            if (o.timing) cudaEventRecord(e1, st);
         }
         if (status != LINGAM_OK) break;
         if (cudaEventRecord(ev[3], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
@@ -286,7 +273,10 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
             rep->t_B_ms = (want_B && cudaEventElapsedTime(&ms, ev[3], ev[4]) == cudaSuccess) ? ms : 0.0;
             double tp = 0.0;
             for (size_t k = 0; k + 1 < pev.size(); k += 2)
-                if (cudaEventElapsedTime(&ms, pev[k], pev[k + 1]) == cudaSuccess) tp += ms;
+                if (cudaEventElapsedTime(&ms, pev[k], pev[k + 1]) == cudaSuccess) {
+                    tp += ms;
+                    if (rep->t_pair_iter_ms && k / 2 < size_t(p)) rep->t_pair_iter_ms[k / 2] = ms;
+                }
             rep->t_pair_ms = tp;
             rep->kernel_launches = launches;
         }

@@ -37,7 +37,7 @@ class Report(ctypes.Structure):
                 ("scores", _c_dbl_p), ("t_standardize_ms", ctypes.c_double), ("t_gram_ms", ctypes.c_double),
                 ("t_order_ms", ctypes.c_double), ("t_B_ms", ctypes.c_double), ("pairs_total", ctypes.c_longlong),
                 ("pairs_unpruned", ctypes.c_longlong), ("t_pair_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("t_pair_iter_ms", _c_dbl_p)]
 
 
 class LingamError(RuntimeError):
@@ -133,6 +133,7 @@ class FitResult:
     pairs_total: int = 0
     pairs_unpruned: int = 0
     kernel_launches: int = 0
+    t_pair_iter_ms: np.ndarray | None = None
 
 
 def _torch():
@@ -199,6 +200,9 @@ def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, for
     rep.pairs_evaluated = pe.ctypes.data_as(_c_ll_p)
     if sc is not None:
         rep.scores = sc.ctypes.data_as(_c_dbl_p)
+    tpi = np.zeros(p) if timing else None
+    if tpi is not None:
+        rep.t_pair_iter_ms = tpi.ctypes.data_as(_c_dbl_p)
     st = L.lingam_fit(ctypes.c_void_p(ptr), p, n, _addr(order), _addr(B) if B is not None else None,
                       ctypes.c_void_p(workspace.data_ptr()), ctypes.byref(o), ctypes.byref(rep))
     del keep, keep_forced
@@ -208,7 +212,7 @@ def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, for
                      times_ms={"standardize": rep.t_standardize_ms, "gram": rep.t_gram_ms,
                                "order": rep.t_order_ms, "B": rep.t_B_ms, "pair": rep.t_pair_ms},
                      pairs_total=int(rep.pairs_total), pairs_unpruned=int(rep.pairs_unpruned),
-                     kernel_launches=int(rep.kernel_launches))
+                     kernel_launches=int(rep.kernel_launches), t_pair_iter_ms=tpi)
 
 
 def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = True, stream=None):
