@@ -124,6 +124,32 @@ __device__ __forceinline__ int scan01(int flag, int* red, int* total) {
     return off + pre;
 }
 
+// Exclusive scans of two 0/1 flags at once; red holds 2 * NTH/32 ints.
+template <int NTH>
+__device__ __forceinline__ void scan01x2(int fa, int fb, int* red, int* pa, int* pb, int* ta, int* tb) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned ma = __ballot_sync(0xffffffffu, fa), mb = __ballot_sync(0xffffffffu, fb);
+    const unsigned below = (1u << lane) - 1u;
+    __syncthreads();
+    if (lane == 0) {
+        red[wid] = __popc(ma);
+        red[NTH / 32 + wid] = __popc(mb);
+    }
+    __syncthreads();
+    int oa = 0, ob = 0, sa = 0, sb = 0;
+    for (int w = 0; w < NTH / 32; ++w) {
+        const int xa = red[w], xb = red[NTH / 32 + w];
+        oa += (w < wid) ? xa : 0;
+        ob += (w < wid) ? xb : 0;
+        sa += xa;
+        sb += xb;
+    }
+    *pa = oa + __popc(ma & below);
+    *pb = ob + __popc(mb & below);
+    *ta = sa;
+    *tb = sb;
+}
+
 template <int NTH, class V>
 __device__ __forceinline__ V block_sum_n(V v, V* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -137,6 +163,20 @@ __device__ __forceinline__ V block_sum_n(V v, V* red) {
     __syncthreads();
     return s;
 }
+
+// Sum of squares in float-float arithmetic: the exact square (TwoProduct) added
+// with TwoSum into a (hi, lo) pair, about 48 bits of precision on the FP32 pipe.
+struct FF {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add_sq(float m) {
+        const float pr = m * m, pe = fmaf(m, m, -pr);
+        const float s = hi + pr, bb = s - hi;
+        const float err = (hi - (s - bb)) + (pr - bb);
+        hi = s;
+        lo += err + pe;
+    }
+    __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
 
 // 16 consecutive values (16-byte aligned) through L2.
 __device__ __forceinline__ void load16_cg(float* v, const float* src) {
@@ -353,20 +393,34 @@ __device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
     const int p = f.p, r = vc->r;
 
     // 1. row contributions: min(0, I(row, col))^2 summed over the wave's columns
-    if (f.reuse)
+    if (f.reuse) {
+#pragma unroll 4
         for (int e = tid; e < nrow; e += NTH) {
             const int v = ld2(f.rows + e);
-            f.part[v] = ld2(f.part + v) + ld2(f.rowsum + e);
+            const double add = ld2(f.rowsum + e);
+            f.part[v] = ld2(f.part + v) + add;
         }
+    }
     __syncthreads();
-    // 2. column contributions max(0, I(row, col))^2 = min(0, I(col, row))^2 in tile order;
+    // 2. column contributions max(0, I(row, col))^2 = min(0, I(col, row))^2 in tile order
+    //    (staged in shared memory by all threads, then summed per column);
     // 3. threshold = lowest complete score (lowest variable index on ties)
+    __shared__ double s_col[32 * 33];
+    double tot = 0.0;
+    for (int t0 = 0; t0 < ntiles; t0 += 32) {
+        for (int k = tid; k < 32 * kTJ; k += NTH) {
+            const int t = t0 + k / kTJ;
+            s_col[(k / kTJ) * 33 + (k % kTJ)] = t < ntiles ? ld2(f.colsum + t * kTJ + (k % kTJ)) : 0.0;
+        }
+        __syncthreads();
+        if (tid < kTJ)
+            for (int j = 0; j < 32 && t0 + j < ntiles; ++j) tot += s_col[j * 33 + tid];
+        __syncthreads();
+    }
     if (tid < 32) {
         double sc = INFINITY;
         int v = 0x7fffffff;
         if (tid < ncol) {
-            double tot = 0.0;
-            for (int t = 0; t < ntiles; ++t) tot += ld2(f.colsum + t * kTJ + tid);
             v = ld2(f.cols + tid);
             sc = ld2(f.part + v) + tot;
             f.part[v] = sc;
@@ -396,57 +450,68 @@ __device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
     __syncthreads();
     const double best = vc->best;
 
-    // 4. prune, then pick the next columns: the first kTJ live un-columned variables
-    //    in candidate order.
-    int nc = 0;
-    for (int base = 0; base < r; base += NTH) {
+    // 4. one pass over the candidates: prune (partial score above the threshold), pick
+    //    the next columns (the first kTJ live un-columned variables in candidate order)
+    //    and list the next rows (every other row-eligible variable: un-columned ones with
+    //    reuse, all remaining ones without), both in candidate order.
+    // The candidates' flags and scores are fetched for all of this thread's positions
+    // first (independent loads), then the blocks are scanned in order.
+    constexpr int kPre = 8;   // positions per thread fetched ahead (r <= kPre * NTH)
+    int pv[kPre], pfl[kPre];
+    double ppart[kPre];
+#pragma unroll
+    for (int j = 0; j < kPre; ++j) {
+        const int k = j * NTH + tid;
+        pv[j] = k < r ? ld2(f.sigma + k) : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < kPre; ++j) {
+        pfl[j] = pv[j] >= 0 ? ld2(f.flags + pv[j]) : 0;
+        ppart[j] = pv[j] >= 0 ? ld2(f.part + pv[j]) : 0.0;
+    }
+    int nlive = 0, nr = 0;
+    for (int base = 0, j = 0; base < r; base += NTH, ++j) {
         const int k = base + tid;
-        int live = 0, v = -1;
+        int live = 0, elig = 0, v = -1, fl = 0;
+        double pt = 0.0;
         if (k < r) {
-            v = ld2(f.sigma + k);
-            int fl = ld2(f.flags + v);
-            if (!(fl & kColumned)) {
-                if (!(fl & kDead) && f.prune && f.reuse && ld2(f.part + v) > best) {
+            if (j < kPre) {
+                v = pv[j];
+                fl = pfl[j];
+                pt = ppart[j];
+            } else {
+                v = ld2(f.sigma + k);
+                fl = ld2(f.flags + v);
+                pt = ld2(f.part + v);
+            }
+            const bool col = (fl & kColumned) != 0;
+            if (!col) {
+                if (!(fl & kDead) && f.prune && f.reuse && pt > best) {
                     fl |= kDead;
                     f.flags[v] = fl;
                 }
                 live = (fl & kDead) ? 0 : 1;
             }
+            elig = f.reuse ? !col : 1;
         }
-        int tot;
-        const int rank = nc + scan01<NTH>(live, red, &tot);
-        if (live && rank < kTJ) {
-            f.cols[rank] = v;
-            f.flags[v] = ld2(f.flags + v) | kPick;
-        }
-        nc += tot;
+        int pl, pe, tl, te;
+        // ranks among live and among eligible variables (a pick is live and eligible)
+        scan01x2<NTH>(live, elig, red, &pl, &pe, &tl, &te);
+        const int lrank = nlive + pl;
+        const bool pick = live && lrank < kTJ;
+        // every pick is eligible; the row rank of an eligible non-pick is the rows listed
+        // so far plus the eligible variables before it in this block minus the picks among them
+        const int picked_before = min(nlive + pl, kTJ) - min(nlive, kTJ);
+        if (pick) f.cols[lrank] = v;
+        if (elig && !pick) f.scratch[nr + pe - picked_before] = v;
+        const int picks_here = min(nlive + tl, kTJ) - min(nlive, kTJ);
+        nlive += tl;
+        nr += te - picks_here;
         __syncthreads();
     }
-    nc = nc < kTJ ? nc : kTJ;
-    __syncthreads();
-    // 5. rows of the next wave: the columns, then every other row-eligible variable
-    //    (un-columned ones with reuse; all remaining ones without) in candidate order.
-    int nr = 0;
-    for (int base = 0; base < r; base += NTH) {
-        const int k = base + tid;
-        int take = 0, v = -1;
-        if (k < r) {
-            v = ld2(f.sigma + k);
-            const int fl = ld2(f.flags + v);
-            take = !(fl & kPick) && (!f.reuse || !(fl & kColumned));
-        }
-        int tot;
-        const int rank = nr + scan01<NTH>(take, red, &tot);
-        if (take) f.scratch[rank] = v;
-        nr += tot;
-        __syncthreads();
-    }
+    const int nc = nlive < kTJ ? nlive : kTJ;
     __syncthreads();
     for (int k = tid; k < nc + nr; k += NTH) f.rows[k] = k < nc ? ld2(f.cols + k) : ld2(f.scratch + k - nc);
-    for (int c = tid; c < nc; c += NTH) {
-        const int v = ld2(f.cols + c);
-        f.flags[v] = ld2(f.flags + v) & ~kPick;
-    }
     __syncthreads();
 
     // 6. no live variable left: the root is the complete variable of lowest score (or
@@ -818,15 +883,19 @@ __device__ __noinline__ void merge_phase(const Fit& f, const Wave& wv, int it, I
 #pragma unroll
             for (int k = 0; k < 32; ++k) acc[k] += v[k];
         }
+        // warp sums to shared memory: lane-major with a pad word (conflict-free both ways)
 #pragma unroll
-        for (int k = 0; k < 32; ++k) scratch[wid * 1024 + lane * 32 + k] = acc[k];
+        for (int k = 0; k < 32; ++k) scratch[wid * 1056 + lane * 33 + k] = acc[k];
         __syncthreads();
         // 2. one thread per pair: warps' sums in warp order, then I
         if (tid < 256) {
             T tot[4] = {T(0), T(0), T(0), T(0)};
             for (int w = 0; w < NW; ++w)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) tot[k] += scratch[w * 1024 + tid * 4 + k];
+                for (int k = 0; k < 4; ++k) {
+                    const int v = tid * 4 + k;   // value index in the item
+                    tot[k] += scratch[w * 1056 + (v >> 5) * 33 + (v & 31)];
+                }
             // pair tid of the item = pair (tid & 3) of compute thread part * 64 + tid / 4
             const int ct = part * 64 + (tid >> 2), q = tid & 3;
             const int e_loc = (ct >> 4) + (q >> 1) * (TI / 2), cc = (ct & 15) + (q & 1) * 16;
@@ -856,27 +925,44 @@ __device__ __noinline__ void merge_phase(const Fit& f, const Wave& wv, int it, I
         if (tid == 0) sh.flag = (atomicAdd(f.tile_cnt + t, 1) == PARTS - 1);
         __syncthreads();
         if (sh.flag) {
-            // 3. the tile's last item: per-row and per-column contributions in FP64
+            // 3. the tile's last item: per-row and per-column contributions in FP64, from the
+            //    tile's I staged in shared memory (row stride kTJ + 1)
             __threadfence();
             const T* It = ibuf + size_t(t) * TI * kTJ;
-            if (tid < TI) {
-                const int e = t * TI + tid;
-                double s = 0.0;
-                for (int cc = 0; cc < kTJ; ++cc) {
-                    const double I = double(__ldcg(It + tid * kTJ + cc));
-                    const double m = I < 0.0 ? I : 0.0;
-                    s = fma(m, m, s);
+            for (int k = tid; k < TI * kTJ; k += CONS) scratch[(k / kTJ) * (kTJ + 1) + (k % kTJ)] = __ldcg(It + k);
+            __syncthreads();
+            if constexpr (kF32) {
+                // squares summed exactly enough (float-float) that a variable's score does not
+                // depend on how its pairs were grouped into tiles and waves
+                if (tid < TI) {
+                    const int e = t * TI + tid;
+                    FF acc;
+                    for (int cc = 0; cc < kTJ; ++cc) acc.add_sq(fminf(scratch[tid * (kTJ + 1) + cc], 0.f));
+                    if (e < nrow) f.rowsum[e] = acc.value();
+                } else if (tid < TI + kTJ) {
+                    const int cc = tid - TI;
+                    FF acc;
+                    for (int e = 0; e < TI; ++e) acc.add_sq(fmaxf(scratch[e * (kTJ + 1) + cc], 0.f));
+                    f.colsum[t * kTJ + cc] = acc.value();
                 }
-                if (e < nrow) f.rowsum[e] = s;
-            } else if (tid < TI + kTJ) {
-                const int cc = tid - TI;
-                double s = 0.0;
-                for (int e = 0; e < TI; ++e) {
-                    const double I = double(__ldcg(It + e * kTJ + cc));
-                    const double m = I > 0.0 ? I : 0.0;
-                    s = fma(m, m, s);
+            } else {
+                if (tid < TI) {
+                    const int e = t * TI + tid;
+                    double s = 0.0;
+                    for (int cc = 0; cc < kTJ; ++cc) {
+                        const double m = fmin(double(scratch[tid * (kTJ + 1) + cc]), 0.0);
+                        s = fma(m, m, s);
+                    }
+                    if (e < nrow) f.rowsum[e] = s;
+                } else if (tid < TI + kTJ) {
+                    const int cc = tid - TI;
+                    double s = 0.0;
+                    for (int e = 0; e < TI; ++e) {
+                        const double m = fmax(double(scratch[e * (kTJ + 1) + cc]), 0.0);
+                        s = fma(m, m, s);
+                    }
+                    f.colsum[t * kTJ + cc] = s;
                 }
-                f.colsum[t * kTJ + cc] = s;
             }
             if (tid == 0) f.tile_cnt[t] = 0;
             __threadfence();
@@ -900,6 +986,7 @@ __device__ __noinline__ void remove_data_phase(const Fit& f, IterShared<T>& sh) 
     Ctl* ctl = f.ctl;
     volatile Ctl* vc = ctl;
     const int r = vc->r, root = vc->root, p = f.p, ld = f.ld, tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
     for (int k = blockIdx.x; k < r; k += gridDim.x) {
         const int w = ld2(f.sigma + k);
         if (tid == 0) f.prev[w] = ld2(f.part + w);
@@ -910,14 +997,22 @@ __device__ __noinline__ void remove_data_phase(const Fit& f, IterShared<T>& sh) 
             }
             continue;
         }
-        const double c = f.sig[size_t(w) * p + root];
-        double om = fma(-c, c, 1.0);
-        if (!(om > 1e-14)) {
-            if (tid == 0) set_status(ctl, LINGAM_EDEGENERATE);
-            om = 1.0;
+        // coefficients of this row, computed once (FP64 is a slow pipe on this GPU)
+        if (tid == 0) {
+            const double c0 = f.sig[size_t(w) * p + root];
+            double om = fma(-c0, c0, 1.0);
+            if (!(om > 1e-14)) {
+                set_status(ctl, LINGAM_EDEGENERATE);
+                om = 1.0;
+            }
+            const double inv0 = 1.0 / sqrt(om);
+            f.inv_root[w] = inv0;
+            sh.dred[30] = c0;
+            sh.dred[31] = inv0;
         }
-        const double inv = 1.0 / sqrt(om);
-        if (tid == 0) f.inv_root[w] = inv;
+        __syncthreads();
+        const double c = sh.dred[30], inv = sh.dred[31];
+        __syncthreads();
         T* xw = static_cast<T*>(f.xt) + size_t(w) * ld;
         const T* xr = static_cast<const T*>(f.xt) + size_t(root) * ld;
         T lcc = T(0), g = T(0);
@@ -925,6 +1020,7 @@ __device__ __noinline__ void remove_data_phase(const Fit& f, IterShared<T>& sh) 
             const float cc = float(c), ii = float(inv);
             float4* xw4 = reinterpret_cast<float4*>(xw);
             const float4* xr4 = reinterpret_cast<const float4*>(xr);
+#pragma unroll 4
             for (int t4 = tid; t4 < ld / 4; t4 += NTH) {
                 const float4 a = xw4[t4], rr = xr4[t4];
                 float4 o;
@@ -946,9 +1042,27 @@ __device__ __noinline__ void remove_data_phase(const Fit& f, IterShared<T>& sh) 
                 if (t < f.n) mom_add(u, lcc, g);
             }
         }
-        const double L = block_sum_n<NTH>(double(lcc), sh.dred);
-        const double Gs = block_sum_n<NTH>(double(g), sh.dred);
-        if (tid == 0) f.hx[w] = hterm(L, Gs, double(f.n));
+        // per-thread sums in the working precision, warp trees, then the warp sums in FP64
+        // by one thread
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lcc += __shfl_xor_sync(0xffffffffu, lcc, o);
+            g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (lane == 0) {
+            sh.dred[wid] = double(lcc);
+            sh.dred[16 + wid] = double(g);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double L = 0.0, Gs = 0.0;
+            for (int k2 = 0; k2 < NTH / 32; ++k2) {
+                L += sh.dred[k2];
+                Gs += sh.dred[16 + k2];
+            }
+            f.hx[w] = hterm(L, Gs, double(f.n));
+        }
+        __syncthreads();
     }
 }
 
@@ -962,16 +1076,16 @@ __device__ __noinline__ void remove_cov_phase(const Fit& f) {
     volatile Ctl* vc = f.ctl;
     const int r = vc->r, root = vc->root, p = f.p, tid = threadIdx.x;
     const double* rootrow = f.sig + size_t(root) * p;
-    for (int a = blockIdx.x; a < r; a += gridDim.x) {
-        const int w = ld2(f.sigma + a);
-        if (w == root) continue;
-        const double cw = rootrow[w], iw = ld2(f.inv_root + w);
+    const int nmine = r > int(blockIdx.x) ? (r - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+    const long long total = (long long)nmine * p;
+#pragma unroll 2
+    for (long long idx = tid; idx < total; idx += NTH) {
+        const int m = int(idx / p), j = int(idx - (long long)m * p);
+        const int w = ld2(f.sigma + blockIdx.x + m * gridDim.x);
+        if (w == root || j == root || !(ld2(f.flags + j) & kAlive)) continue;
         double* row = f.sig + size_t(w) * p;
-        for (int j = tid; j < p; j += NTH) {
-            if (j == root || !(ld2(f.flags + j) & kAlive)) continue;
-            if (j == w) row[j] = 1.0;
-            else row[j] = (row[j] - cw * rootrow[j]) * (iw * ld2(f.inv_root + j));
-        }
+        if (j == w) row[j] = 1.0;
+        else row[j] = (row[j] - rootrow[w] * rootrow[j]) * (ld2(f.inv_root + w) * ld2(f.inv_root + j));
     }
 }
 
