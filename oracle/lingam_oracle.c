@@ -84,6 +84,32 @@ int oracle_standardize(const double* x, long n, double* out) {
     return ORACLE_OK;
 }
 
+/* CalculateCovMat (Algorithm 3) by its definition: every row normalised as
+ * above, then Sigma[i][j] = sum_t xn_i[t] xn_j[t] / (n-1), both triangles
+ * computed (the diagonal too, so it is 1 only up to rounding).  X is p x n
+ * row-major, out p x p row-major. */
+int oracle_covariance(const double* X, int p, long n, double* out) {
+    double* Z = (double*)malloc(sizeof(double) * (size_t)p * (size_t)n);
+    if (!Z) return ORACLE_ENOMEM;
+    for (int i = 0; i < p; ++i) {
+        int st = oracle_standardize(X + (size_t)i * n, n, Z + (size_t)i * n);
+        if (st != ORACLE_OK) {
+            free(Z);
+            return st;
+        }
+    }
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j < p; ++j) {
+            const double* zi = Z + (size_t)i * n;
+            const double* zj = Z + (size_t)j * n;
+            double s = 0.0;
+            for (long t = 0; t < n; ++t) s += zi[t] * zj[t];
+            out[(size_t)i * p + j] = s / (double)(n - 1);
+        }
+    free(Z);
+    return ORACLE_OK;
+}
+
 /* Eq. HApp on an already normalised sample u. */
 double oracle_entropy(const double* u, long n) {
     double lc = 0.0, g = 0.0;

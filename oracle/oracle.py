@@ -67,6 +67,7 @@ def _declare(L):
         getattr(L, name).restype = ctypes.c_double
         getattr(L, name).argtypes = []
     L.oracle_standardize.argtypes = [dp, ctypes.c_long, dp]
+    L.oracle_covariance.argtypes = [dp, ctypes.c_int, ctypes.c_long, dp]
     L.oracle_entropy.argtypes = [dp, ctypes.c_long]
     L.oracle_entropy.restype = ctypes.c_double
     L.oracle_regress.argtypes = [dp, dp, ctypes.c_long, dp]
@@ -108,6 +109,17 @@ def standardize(x, lib=None) -> np.ndarray:
     st = (lib or _get()).oracle_standardize(_d(x), x.size, _d(out))
     if st != OK:
         raise OracleError(st, "standardize")
+    return out
+
+
+def covariance(X, lib=None) -> np.ndarray:
+    """CalculateCovMat (Algorithm 3): covariance of the normalised rows of X (p x n)."""
+    X = _rows(X)
+    p, n = X.shape
+    out = np.empty((p, p))
+    st = (lib or _get()).oracle_covariance(_d(X), p, n, _d(out))
+    if st != OK:
+        raise OracleError(st, "covariance")
     return out
 
 
@@ -202,7 +214,7 @@ def variable_scores(X, prefix, vars_, nthreads: int = 0, lib=None) -> np.ndarray
 class View:
     """The module's functions bound to one loaded oracle library (e.g. a test build)."""
 
-    _names = ("constants", "num_threads", "standardize", "entropy", "regress", "pair_measure", "pair_measures",
+    _names = ("constants", "num_threads", "standardize", "covariance", "entropy", "regress", "pair_measure", "pair_measures",
               "find_root_scores", "fit_B", "fit", "variable_scores")
 
     def __init__(self, lib):

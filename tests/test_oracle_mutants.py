@@ -37,6 +37,9 @@ MUTANTS = {
                                "st = oracle_regress(W + (size_t)root * n, W + (size_t)w * n, n, tmp);"),
     "no_regress_root": ("if (st == ORACLE_OK) memcpy(W + (size_t)w * n, tmp, sizeof(double) * (size_t)n);",
                         "(void)tmp;"),
+    "covariance_wrong_operand": ("for (long t = 0; t < n; ++t) s += zi[t] * zj[t];",
+                                 "for (long t = 0; t < n; ++t) s += zi[t] * zi[t];"),
+    "covariance_divisor_n": ("out[(size_t)i * p + j] = s / (double)(n - 1);", "out[(size_t)i * p + j] = s / (double)n;"),
     "B_wrong_predecessor_index": ("for (int a = 0; a < k; ++a) B[(size_t)tgt * p + K[a]] = rhs[a];",
                                   "for (int a = 0; a < k; ++a) B[(size_t)tgt * p + a] = rhs[a];"),
     "B_transposed_store": ("for (int a = 0; a < k; ++a) B[(size_t)tgt * p + K[a]] = rhs[a];",

@@ -159,6 +159,20 @@ def test_residual_variance_closed_form(oracle_mod):
     assert np.allclose(oracle_mod.standardize(r), (zi - rho * zj) / math.sqrt(1 - rho * rho), rtol=0, atol=1e-12)
 
 
+def test_covariance_matrix_is_the_correlation_matrix(oracle_mod):
+    # CalculateCovMat (Algorithm 3) on normalised rows is the sample correlation
+    # matrix, whatever divisor the normalisation uses: numpy's corrcoef fixes it
+    d = synth.workload("p20_n2000", seed=3)
+    S = oracle_mod.covariance(d.X)
+    C = np.corrcoef(d.X)
+    assert S.shape == (20, 20)
+    assert np.abs(S - C).max() < 1e-12
+    assert np.abs(np.diag(S) - 1.0).max() < 1e-12
+    # a row subset gives the matching sub-block (rows are normalised one by one)
+    sub = [4, 11, 17]
+    assert np.abs(oracle_mod.covariance(d.X[sub]) - S[np.ix_(sub, sub)]).max() < 1e-14
+
+
 def test_covariance_update_closed_form(oracle_mod):
     d = synth.workload("p20_n2000", seed=4)
     z = [oracle_mod.standardize(d.X[k]) for k in (1, 5, 9)]
