@@ -42,7 +42,8 @@ extern "C" {
 typedef enum {
     LINGAM_OK = 0,
     LINGAM_EINVAL = -1,       /* bad argument: p < 1, n < 3, NULL pointer, bad option, workspace too small */
-    LINGAM_EDEGENERATE = -2,  /* zero variance row or residual, |rho| >= 1, non-finite data */
+    LINGAM_EDEGENERATE = -2,  /* zero variance row or residual, non-finite data, or a pair with
+                                 1 - rho^2 <= 2^-20 (mixed path) / 1e-14 (FP64 path): collinear */
     LINGAM_ENOMEM = -3,       /* reserved: the library itself never allocates */
     LINGAM_ECUDA = -4,        /* a CUDA runtime call or kernel launch failed */
     LINGAM_ETIMEOUT = -5      /* a bounded device-side wait ran out (opts.timeout_s) */
@@ -116,6 +117,22 @@ size_t lingam_workspace_size(long long p, long long n, const lingam_opts* opts);
  */
 int lingam_fit(const void* X, long long p, long long n, int* order, double* B, void* workspace,
                const lingam_opts* opts, lingam_report* report);
+
+/*
+ * lingam_covariance -- NormalizeData and CalculateCovMat of Algorithm 3 alone: the
+ * covariance matrix of the normalised rows, Sigma = Xn Xn^T / (n-1), where row i of Xn
+ * is (X_i - mean) / sd with the divisor n-1 in the variance (Eq. var_update).
+ *   X, p, n, workspace, opts  as in lingam_fit (opts->forced_order must be NULL).
+ *   Sigma      [p*p] doubles, host or device, row-major; Sigma[i*p + i] = 1 exactly.
+ *   report     NULL, or a report whose t_standardize_ms, t_gram_ms and kernel_launches
+ *              are filled in (the other fields are left untouched).
+ * precision LINGAM_MIXED computes the product on the tensor cores from a TF32 + FP32
+ * split of the FP32 rows (FP32 accumulation, FP64 sum of the sample-axis splits);
+ * LINGAM_FP64 computes it in FP64.  Sigma is written only on LINGAM_OK; rows with zero
+ * variance or non-finite values give LINGAM_EDEGENERATE.
+ */
+int lingam_covariance(const void* X, long long p, long long n, double* Sigma, void* workspace,
+                      const lingam_opts* opts, lingam_report* report);
 
 /* Workspace for lingam_fit_batch over `count` datasets of sizes p[k] x n[k]. */
 size_t lingam_workspace_size_batch(int count, const long long* p, const long long* n, const lingam_opts* opts);

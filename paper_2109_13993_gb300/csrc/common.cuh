@@ -31,6 +31,10 @@ constexpr int kChunk64 = 64;           // samples per stage (FP64 path)
 constexpr int kSub = 32;               // samples per product group (one lg2 per group)
 constexpr int kStages = 3;             // TMA ring depth
 constexpr int kSampleAlign = 128;      // n is padded with zero samples to a multiple of this
+// A pair with 1 - rho^2 at or below this bound is degenerate (collinear to the working
+// precision): on the mixed path the rows are FP32 and Sigma is exact only to about 1e-9,
+// so a correlation within 2^-21 of +-1 cannot be told apart from an exact one.
+__host__ __device__ constexpr double degenerate_om(bool f32) { return f32 ? 0x1p-20 : 1e-14; }
 constexpr int kMaxSplit = 64;
 
 // Flags per variable (ctl->flags[v]).

@@ -1,4 +1,4 @@
-// k_gram.cu -- CalculateCovMat (Algorithm 3, line 4): Sigma = Xn Xn^T / (n-1)
+// k_gram.cu -- CalculateCovMat (Algorithm 3): Sigma = Xn Xn^T / (n-1)
 // of the normalised rows, the covariance the closed forms of Sec. III-E start
 // from.  SIMT version: 64 x 64 output tiles of the upper triangle, K-chunks of
 // 32 samples staged in shared memory; FP32 products with FP32 chunk sums

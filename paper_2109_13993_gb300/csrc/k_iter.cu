@@ -358,7 +358,7 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
         ctl->best_var = -1;
         ctl->pairs_it = 0;
         if (r <= 1) {
-            // Algorithm 2, lines 1-3: a single variable is the root
+            // Algorithm 2: a single remaining variable is the root
             const int root = r == 1 ? f.sigma[0] : -1;
             ctl->root = root;
             ctl->done = 1;
@@ -675,7 +675,7 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
             if (okp) okp = f.reuse ? (e >= ncol || c < e) : (vi != vj);
             double rho = okp ? f.sig[size_t(vi) * p + vj] : 0.0;
             double om = fma(-rho, rho, 1.0);   // 1 - rho^2 in FP64
-            if (okp && !(om > 1e-14)) {
+            if (okp && !(om > degenerate_om(kF32))) {
                 set_status(ctl, LINGAM_EDEGENERATE);
                 om = 1.0;
                 rho = 0.0;
@@ -1001,7 +1001,7 @@ __device__ __noinline__ void remove_data_phase(const Fit& f, IterShared<T>& sh) 
         if (tid == 0) {
             const double c0 = f.sig[size_t(w) * p + root];
             double om = fma(-c0, c0, 1.0);
-            if (!(om > 1e-14)) {
+            if (!(om > degenerate_om(std::is_same<T, float>::value))) {
                 set_status(ctl, LINGAM_EDEGENERATE);
                 om = 1.0;
             }

@@ -1,4 +1,4 @@
-// k_rows.cu -- NormalizeData (Algorithm 3, line 3): per-row normalisation of
+// k_rows.cu -- NormalizeData (Algorithm 3): per-row normalisation of
 // the input with the first H(x) terms.
 #include <type_traits>
 

@@ -11,11 +11,19 @@ namespace lingam {
 cudaError_t ensure_smem_attr(const void* func, size_t bytes);
 
 
-// Normalise the rows of the input (Alg. 3 line 3), write the padded working copy,
+// Normalise the rows of the input (NormalizeData, Algorithm 3), write the padded working copy,
 // the row moments and H(x) - H(nu).
 cudaError_t launch_standardize(const Fit& f, const void* x, int input_dtype, cudaStream_t st);
-// Sigma = Xn Xn^T / (n-1) of the normalised rows (Alg. 3 line 4); sig0 = sig.
+// Sigma = Xn Xn^T / (n-1) of the normalised rows (CalculateCovMat, Algorithm 3); sig0 = sig.
 cudaError_t launch_gram(const Fit& f, cudaStream_t st);
+// The same product on the tensor cores (mixed path): the rows are split into exact
+// TF32 digits (three p x ld float planes and p exponents in `digits`), tcgen05 MMAs
+// over 128 x 128 tiles of the upper triangle with the sample axis split over CTAs,
+// float-float partial tiles in `partial`, summed in FP64 into sig and sig0.
+cudaError_t launch_gram_tc(const Fit& f, void* digits, void* partial, cudaStream_t st);
+// Bytes of `digits` and of `partial` that launch_gram_tc needs for p variables and row length ld.
+size_t gram_tc_digit_bytes(long long p, int ld);
+size_t gram_tc_partial_bytes(long long p, int ld);
 // One iteration of Algorithm 3 (ParaFindRoot, UpdateData, UpdateCovMat) as one
 // persistent cooperative launch; grid = SMs.
 cudaError_t launch_iteration(const Fit& f, int it, int grid, cudaStream_t st);

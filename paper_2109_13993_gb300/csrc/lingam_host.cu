@@ -63,7 +63,10 @@ static Layout make_layout(long long p, long long n, int precision, int input_dty
     };
     const size_t P = size_t(p), PP = size_t(p) * size_t(p);
     L.off_ctl = take(sizeof(Ctl));
-    L.off_xin = take(P * size_t(n) * in_esz);
+    // the host-input copy is dead once the rows are normalised; the mixed path's
+    // tensor-core Gram reuses it for the digit planes of its operands
+    const size_t split_bytes = precision == LINGAM_MIXED ? gram_tc_digit_bytes(p, L.ld) : 0;
+    L.off_xin = take(std::max(P * size_t(n) * in_esz, split_bytes));
     L.off_xt = take(P * size_t(L.ld) * L.esz);
     L.off_mu = take(P * 8);
     L.off_sd = take(P * 8);
@@ -84,7 +87,10 @@ static Layout make_layout(long long p, long long n, int precision, int input_dty
     // one partial-moment slot per (tile, CTA) segment; slot index tile + CTA, and a wave never
     // uses more CTAs than it has (tile, chunk) units
     const size_t units = size_t(L.maxtiles) * size_t(L.ld / chunk_of(precision));
-    L.off_partials = take((size_t(L.maxtiles) + std::min(size_t(kMaxGrid), units)) * kPairThreads * 16 * L.esz);
+    // (the Gram's split partial tiles use the same region before the first iteration)
+    const size_t pair_partials = (size_t(L.maxtiles) + std::min(size_t(kMaxGrid), units)) * kPairThreads * 16 * L.esz;
+    L.off_partials =
+        take(std::max(pair_partials, precision == LINGAM_MIXED ? gram_tc_partial_bytes(p, L.ld) : size_t(0)));
     L.off_invroot = take(P * 8);
     L.off_tilecnt = take(size_t(L.maxtiles) * 4);
     L.off_ibuf = take(size_t(L.maxtiles) * 64 * kTJ * L.esz);
@@ -115,9 +121,10 @@ static bool is_device_ptr(const void* ptr) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// cov_out != nullptr: stop after CalculateCovMat and copy Sigma (p x p) there.
 static int fit_one(const void* X, long long p_, long long n_, int* order, double* B, void* workspace,
-                   const lingam_opts& o, lingam_report* rep) {
-    if (!X || !order || !workspace || p_ < 1 || n_ < 3 || p_ > kMaxP || n_ > (1ll << 30) || !valid_opts(o))
+                   const lingam_opts& o, lingam_report* rep, double* cov_out = nullptr) {
+    if (!X || !(order || cov_out) || !workspace || p_ < 1 || n_ < 3 || p_ > kMaxP || n_ > (1ll << 30) || !valid_opts(o))
         return LINGAM_EINVAL;
     if (!is_device_ptr(workspace) || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return LINGAM_EINVAL;
     const int p = int(p_), n = int(n_);
@@ -220,9 +227,22 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
         if (cudaEventRecord(ev[0], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
         if (launch_standardize(f, xdev, o.input_dtype, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
         if (cudaEventRecord(ev[1], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
-        if (launch_gram(f, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+        if (o.precision == LINGAM_MIXED) {
+            if (launch_gram_tc(f, base + L.off_xin, f.partials, st) != cudaSuccess) {
+                status = LINGAM_ECUDA;
+                break;
+            }
+            launches += 4;
+        } else {
+            if (launch_gram(f, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+            launches += 2;
+        }
         if (cudaEventRecord(ev[2], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
-        launches += 2;
+        if (cov_out) {
+            cudaEventRecord(ev[3], st);
+            cudaEventRecord(ev[4], st);
+            break;
+        }
         const int grid = iteration_grid(f, nsm);
         if (grid < 1) {
             status = LINGAM_ECUDA;
@@ -255,7 +275,15 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
         if (cudaMemcpy(&ch, f.ctl, sizeof(ch), cudaMemcpyDeviceToHost) != cudaSuccess) status = LINGAM_ECUDA;
         else if (ch.status != 0) status = ch.status;
     }
-    if (status == LINGAM_OK) {
+    if (status == LINGAM_OK && cov_out) {
+        if (cudaMemcpy(cov_out, f.sig, size_t(p) * p * 8, cudaMemcpyDefault) != cudaSuccess) status = LINGAM_ECUDA;
+        if (rep && status == LINGAM_OK) {
+            float ms = 0.f;
+            rep->t_standardize_ms = cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess ? ms : -1.0;
+            rep->t_gram_ms = cudaEventElapsedTime(&ms, ev[1], ev[2]) == cudaSuccess ? ms : -1.0;
+            rep->kernel_launches = launches;
+        }
+    } else if (status == LINGAM_OK) {
         // outputs (cudaMemcpyDefault: host or device destinations)
         if (cudaMemcpyAsync(order, f.order, size_t(p) * 4, cudaMemcpyDefault, st) != cudaSuccess) status = LINGAM_ECUDA;
         if (want_B && cudaMemcpyAsync(B, f.bout, size_t(p) * p * 8, cudaMemcpyDefault, st) != cudaSuccess)
@@ -334,6 +362,15 @@ int lingam_fit(const void* X, long long p, long long n, int* order, double* B, v
     return fit_one(X, p, n, order, B, workspace, o, report);
 }
 
+int lingam_covariance(const void* X, long long p, long long n, double* Sigma, void* workspace,
+                      const lingam_opts* opts, lingam_report* report) {
+    lingam_opts o;
+    lingam_default_opts(&o);
+    if (opts) o = *opts;
+    if (!Sigma || o.forced_order) return LINGAM_EINVAL;
+    return fit_one(X, p, n, nullptr, nullptr, workspace, o, report, Sigma);
+}
+
 size_t lingam_workspace_size_batch(int count, const long long* p, const long long* n, const lingam_opts* opts) {
     if (count < 0 || (count > 0 && (!p || !n))) return 0;
     size_t tot = 0;
@@ -370,7 +407,7 @@ const char* lingam_status_string(int s) {
     switch (s) {
         case LINGAM_OK: return "ok";
         case LINGAM_EINVAL: return "invalid argument";
-        case LINGAM_EDEGENERATE: return "degenerate data (zero variance, |rho| >= 1 or non-finite value)";
+        case LINGAM_EDEGENERATE: return "degenerate data (zero variance, collinear pair or non-finite value)";
         case LINGAM_ENOMEM: return "out of memory";
         case LINGAM_ECUDA: return "CUDA error";
         case LINGAM_ETIMEOUT: return "device-side wait timed out";

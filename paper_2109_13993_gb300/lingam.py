@@ -79,6 +79,9 @@ def load():
     L.lingam_fit_static.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.POINTER(Report)]
     L.lingam_fit_static.restype = ctypes.c_int
+    L.lingam_covariance.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.POINTER(Report)]
+    L.lingam_covariance.restype = ctypes.c_int
     L.lingam_status_string.argtypes = [ctypes.c_int]
     L.lingam_status_string.restype = ctypes.c_char_p
     _lib = L
@@ -213,6 +216,32 @@ def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, for
                                "order": rep.t_order_ms, "B": rep.t_B_ms, "pair": rep.t_pair_ms},
                      pairs_total=int(rep.pairs_total), pairs_unpruned=int(rep.pairs_unpruned),
                      kernel_launches=int(rep.kernel_launches), t_pair_iter_ms=tpi)
+
+
+def covariance(X, precision: str = "mixed", stream=None, workspace=None, out=None):
+    """lingam_covariance: Sigma (p x p, float64) of the normalised rows of X, and the
+    report's {"standardize", "gram"} times in ms.  `out` may be a float64 numpy array
+    or a CUDA tensor (p x p) to write Sigma into."""
+    L = load()
+    ptr, p, n, dt, keep = _data_ptr(X)
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    o, _ = make_opts(precision, dt, stream=stream)
+    need = int(L.lingam_workspace_size(p, n, ctypes.byref(o)))
+    if need == 0:
+        raise LingamError(LINGAM_EINVAL, "invalid sizes or options")
+    if workspace is None or workspace.numel() < need:
+        workspace = alloc_workspace(need)
+    S = out if out is not None else np.zeros((p, p))
+    rep = Report()
+    st = L.lingam_covariance(ctypes.c_void_p(ptr), p, n, ctypes.c_void_p(_addr(S)),
+                             ctypes.c_void_p(workspace.data_ptr()), ctypes.byref(o), ctypes.byref(rep))
+    del keep
+    if st != LINGAM_OK:
+        raise LingamError(st, status_string(st))
+    return S, {"standardize": rep.t_standardize_ms, "gram": rep.t_gram_ms,
+               "kernel_launches": int(rep.kernel_launches)}
 
 
 def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = True, stream=None):

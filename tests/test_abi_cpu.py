@@ -40,7 +40,7 @@ def test_workspace_size(lib):
     a = lingam.workspace_size(100, 10000)
     b = lingam.workspace_size(1000, 10000)
     c = lingam.workspace_size(1000, 10000, precision="fp64")
-    assert 0 < a < b < c
+    assert 0 < a < b and a < c   # the mixed path also holds the Gram's digit planes
     assert b % 256 == 0
     assert lingam.workspace_size(0, 100) == 0
     assert lingam.workspace_size(10, 2) == 0
