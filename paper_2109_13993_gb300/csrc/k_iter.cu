@@ -554,7 +554,7 @@ __device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
 // ------------------------------------------------------------------ per-sample math (FP32)
 // Two consecutive samples of one residual u' (scaled by kScale).
 struct Acc2 {
-    float2 A, P, G;   // sum of kC3 |u'|, product of (1 + e^{-2|u|}), sum of u' e^{-u^2/2}; per half
+    float2 A, P, G;   // sum of |kC3 u'|, product of (1 + e^{-2|u|}), sum of u' e^{-u^2/2}; per half
 };
 __device__ __forceinline__ void acc2_add(Acc2& s, float2 u) {
     const float2 q = __fmul2_rn(u, u);
@@ -562,54 +562,14 @@ __device__ __forceinline__ void acc2_add(Acc2& s, float2 u) {
     g.x = ex2_approx(-q.x);
     g.y = ex2_approx(-q.y);
     s.G = __ffma2_rn(u, g, s.G);
-    float2 t;
-    t.x = fabsf(u.x) * kC3;
-    t.y = fabsf(u.y) * kC3;
+    // y = kC3 u' (kC3 < 0): e^{-2|u|} = 2^{-|y|}, the sign and the absolute value being
+    // operand modifiers of the exponential
+    const float2 y = __fmul2_rn(u, make_float2(kC3, kC3));
     float2 e;
-    e.x = ex2_approx(t.x);
-    e.y = ex2_approx(t.y);
+    e.x = ex2_approx(-fabsf(y.x));
+    e.y = ex2_approx(-fabsf(y.y));
     s.P = __ffma2_rn(s.P, e, s.P);
-    s.A = __fadd2_rn(s.A, t);
-}
-
-// ------------------------------------------------------------------ copy ring
-// Warp-cooperative: lane 0 posts the expected bytes, the lanes issue one 1-D bulk
-// copy per variable of the tile (rows then columns) for one chunk of samples.
-template <class T>
-__device__ __forceinline__ void issue_chunk(const Fit& f, T* stage, uint64_t* bar, long long unit, int nch, int nrow,
-                                            int ncol) {
-    using Cfg = PairCfg<T>;
-    constexpr int CH = Cfg::CH, LDS = Cfg::LDS, TI = Cfg::TI;
-    constexpr int SLOTS = (TI + kTJ + 31) / 32;
-    const int lane = threadIdx.x & 31;
-    const int t = int(unit / nch), c = int(unit % nch);
-    const T* xt = static_cast<const T*>(f.xt);
-    const size_t t0 = size_t(c) * CH;
-    int vars[SLOTS];
-    int nvalid = 0;
-#pragma unroll
-    for (int k = 0; k < SLOTS; ++k) {
-        const int slot = lane + 32 * k;
-        int v = -1;
-        if (slot < TI) {
-            const int row = t * TI + slot;
-            v = row < nrow ? ld2(f.rows + row) : -1;
-        } else if (slot < TI + kTJ) {
-            v = (slot - TI) < ncol ? ld2(f.cols + slot - TI) : -1;
-        }
-        vars[k] = v;
-        nvalid += __popc(__ballot_sync(0xffffffffu, v >= 0));
-    }
-    if (lane == 0) {
-        fence_proxy_async();
-        mbar_expect_tx(bar, uint32_t(nvalid) * CH * sizeof(T));
-    }
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < SLOTS; ++k) {
-        const int slot = lane + 32 * k;
-        if (vars[k] >= 0) bulk_g2s(stage + slot * LDS, xt + size_t(vars[k]) * f.ld + t0, CH * sizeof(T), bar);
-    }
+    s.A = __fadd2_rn(s.A, make_float2(fabsf(y.x), fabsf(y.y)));
 }
 
 // Shared state of one CTA (besides the dynamic copy ring).
@@ -621,7 +581,69 @@ struct IterShared {
     int abort;
     int flag;
     double dred[32];
+    // the variables of the copy rows (tile rows, then the wave's columns) of the two
+    // most recent tiles a chunk was issued for, and how many of them are valid
+    int tvars[2][64 + kTJ];
+    int tvalid[2];
+    int ttag[2];
 };
+
+// ------------------------------------------------------------------ copy ring
+// Warp-cooperative: lane 0 posts the expected bytes, the lanes issue one 1-D bulk
+// copy per variable of the tile (rows then columns) for one chunk of samples.  The
+// variables of a tile are read from global memory once and kept in shared memory
+// (two tile slots): chunks are issued one warp at a time (the release chain orders
+// the issuing warps) and in increasing tile order within a wave.
+template <class T>
+__device__ __forceinline__ void issue_chunk(const Fit& f, IterShared<T>& sh, T* stage, uint64_t* bar,
+                                            long long unit, int nch, int nrow, int ncol) {
+    using Cfg = PairCfg<T>;
+    constexpr int CH = Cfg::CH, LDS = Cfg::LDS, TI = Cfg::TI;
+    constexpr int SLOTS = (TI + kTJ + 31) / 32;
+    static_assert(TI + kTJ <= 64 + kTJ, "tile variable cache too small");
+    const int lane = threadIdx.x & 31;
+    const int t = int(unit / nch), c = int(unit % nch);
+    const int cs = t & 1;
+    const T* xt = static_cast<const T*>(f.xt);
+    const size_t t0 = size_t(c) * CH;
+    volatile int* tag = sh.ttag;
+    if (__shfl_sync(0xffffffffu, tag[cs], 0) != t) {
+        int nv = 0;
+#pragma unroll
+        for (int k = 0; k < SLOTS; ++k) {
+            const int slot = lane + 32 * k;
+            int v = -1;
+            if (slot < TI) {
+                const int row = t * TI + slot;
+                v = row < nrow ? ld2(f.rows + row) : -1;
+            } else if (slot < TI + kTJ) {
+                v = (slot - TI) < ncol ? ld2(f.cols + slot - TI) : -1;
+            }
+            if (slot < TI + kTJ) sh.tvars[cs][slot] = v;
+            nv += __popc(__ballot_sync(0xffffffffu, v >= 0));
+        }
+        if (lane == 0) sh.tvalid[cs] = nv;
+        __syncwarp();
+        if (lane == 0) tag[cs] = t;
+        __syncwarp();
+    }
+    int vars[SLOTS];
+#pragma unroll
+    for (int k = 0; k < SLOTS; ++k) {
+        const int slot = lane + 32 * k;
+        vars[k] = slot < TI + kTJ ? sh.tvars[cs][slot] : -1;
+    }
+    if (lane == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(bar, uint32_t(sh.tvalid[cs]) * CH * sizeof(T));
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < SLOTS; ++k) {
+        const int slot = lane + 32 * k;
+        if (vars[k] >= 0) bulk_g2s(stage + slot * LDS, xt + size_t(vars[k]) * f.ld + t0, CH * sizeof(T), bar);
+    }
+}
 
 // ------------------------------------------------------------------ compute phase
 // Returns false when a wait gave up (the CTA then leaves the kernel).
@@ -639,21 +661,30 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
     Ctl* ctl = f.ctl;
     const int ntiles = wv.ntiles, ncol = wv.ncol, nrow = wv.nrow;
     const int p = f.p;
+    // stream-K over 32-sample groups: a CTA's range of (tile, group) units may start and
+    // end inside a chunk; it stages every chunk it touches, [c_lo, c_hi) in global chunk
+    // index (tile * nch + chunk = group / GPC)
+    constexpr int GPC = CH / kSub;
     const int nch = f.ld / CH;
-    const long long U = (long long)ntiles * nch, G = working_ctas(U, gridDim.x);
+    const long long ng = (long long)nch * GPC;   // groups per tile
+    const long long U = (long long)ntiles * ng, G = working_ctas(U, gridDim.x);
     const int b = blockIdx.x;
     if (b >= G) return true;   // no unit for this CTA in this wave
-    const long long u_lo = unit_lo(b, U, G), u_hi = unit_lo(b + 1, U, G);
-    const int total = int(u_hi - u_lo);
+    const long long g_lo = unit_lo(b, U, G), g_hi = unit_lo(b + 1, U, G);
+    const long long c_lo = g_lo / GPC;
+    const int total = int((g_hi - 1) / GPC + 1 - c_lo);
     const int tid = threadIdx.x, lane = tid & 31;
     const unsigned long long tmo = ctl->timeout_ns;
     const int base = chunk_base;   // ring position of this wave's first chunk
 
-    if (tid < 32)
+    if (tid < 32) {
+        if (lane < 2) sh.ttag[lane] = -1;   // the rows and columns changed with the wave
+        __syncwarp();
         for (int k = 0; k < min(total, kStages); ++k) {
             const int s = (base + k) % kStages;
-            issue_chunk<T>(f, ring + size_t(s) * stage_elems<T>(), &full[s], u_lo + k, nch, nrow, ncol);
+            issue_chunk<T>(f, sh, ring + size_t(s) * stage_elems<T>(), &full[s], c_lo + k, nch, nrow, ncol);
         }
+    }
     if (tid == 0) sh.issued = min(total, kStages);
 
     const int ty = tid >> 4, tx = tid & 15;
@@ -662,9 +693,9 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
     T* parts = static_cast<T*>(f.partials);
     int k = 0;   // chunk index within this wave (this CTA)
     bool ok = true;
-    for (long long u = u_lo; u < u_hi;) {
-        const int t = int(u / nch), c0 = int(u % nch);
-        const int c1 = int(min((long long)nch, c0 + (u_hi - u)));
+    for (long long u = g_lo; u < g_hi;) {
+        const int t = int(u / ng);
+        const long long seg_end = min(g_hi, (long long)(t + 1) * ng);   // this CTA's groups of tile t
         T s_[4], sr_[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -697,7 +728,11 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
             D[j] = T(0);
             Gt[j] = T(0);
         }
-        for (int c = c0; c < c1; ++c, ++k) {
+        for (long long g = u; g < seg_end; ++k) {
+            const long long cg = g / GPC;   // global chunk index; k == cg - c_lo
+            const int tt0 = int(g - cg * GPC) * kSub;
+            const int tt1 = int(min(seg_end, (cg + 1) * GPC) - cg * GPC) * kSub;
+            g = min(seg_end, (cg + 1) * GPC);
             const int pos = base + k;
             const int s = pos % kStages;
             if (!mbar_wait_or_abort(&full[s], (pos / kStages) & 1, ctl, tmo, &sh.abort)) {
@@ -718,7 +753,7 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
                     sr2[q] = make_float2(-sr_[q], -sr_[q]);
                 }
 #pragma unroll 1
-                for (int tt = 0; tt < CH; tt += kSub) {
+                for (int tt = tt0; tt < tt1; tt += kSub) {
                     Acc2 acc[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -749,18 +784,18 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
                         }
                     }
                     // close the group: one lg2 per residual for both halves' products;
-                    // sum |u| = (sum kC3 |u'|) / (kC3 kScale)
+                    // sum |u| = (sum |kC3 u'|) / (-kC3 kScale)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const float lsum = lg2_approx(acc[j].P.x * acc[j].P.y);
                         const float asum = acc[j].A.x + acc[j].A.y;
-                        D[j] += fmaf(float(kLn2), lsum, fmaf(asum, kInvScale / kC3, grp_off));
+                        D[j] += fmaf(float(kLn2), lsum, fmaf(asum, kInvScale / -kC3, grp_off));
                         Gt[j] += acc[j].G.x + acc[j].G.y;
                     }
                 }
             } else {
 #pragma unroll 1
-                for (int tt = 0; tt < CH; tt += kSub) {
+                for (int tt = tt0; tt < tt1; tt += kSub) {
                     T A[8], P[8], Gs[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -807,8 +842,8 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
             last = __shfl_sync(0xffffffffu, last, 0);
             if (last && k + kStages < total) {
                 const int s2i = (pos + kStages) % kStages;
-                issue_chunk<T>(f, ring + size_t(s2i) * stage_elems<T>(), &full[s2i], u_lo + k + kStages, nch, nrow,
-                               ncol);
+                issue_chunk<T>(f, sh, ring + size_t(s2i) * stage_elems<T>(), &full[s2i], c_lo + k + kStages, nch,
+                               nrow, ncol);
                 if (lane == 0) atomicMax(&sh.issued, k + kStages + 1);
             }
         }
@@ -835,7 +870,7 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
             dst[4 * q + 2] = D[2 * q + 1];
             dst[4 * q + 3] = Gt[2 * q + 1];
         }
-        u += c1 - c0;
+        u = seg_end;
     }
     chunk_base = base + total;
     return true;
@@ -859,8 +894,9 @@ __device__ __noinline__ void merge_phase(const Fit& f, const Wave& wv, int it, I
     constexpr bool kF32 = std::is_same<T, float>::value;
     Ctl* ctl = f.ctl;
     const int ntiles = wv.ntiles, ncol = wv.ncol, nrow = wv.nrow;
-    const int ld = f.ld, nch = ld / CH;
-    const long long U = (long long)ntiles * nch, G = working_ctas(U, gridDim.x);
+    const int ld = f.ld;
+    const long long ng = ld / kSub;   // 32-sample groups per tile: the stream-K unit
+    const long long U = (long long)ntiles * ng, G = working_ctas(U, gridDim.x);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const T* parts = static_cast<const T*>(f.partials);
     T* ibuf = static_cast<T*>(f.ibuf);
@@ -869,8 +905,8 @@ __device__ __noinline__ void merge_phase(const Fit& f, const Wave& wv, int it, I
     const int nitems = ntiles * PARTS;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int t = item / PARTS, part = item % PARTS;
-        const int b_first = cta_of_unit((long long)t * nch, U, G);
-        const int b_last = cta_of_unit((long long)(t + 1) * nch - 1, U, G);
+        const int b_first = cta_of_unit((long long)t * ng, U, G);
+        const int b_last = cta_of_unit((long long)(t + 1) * ng - 1, U, G);
         // 1. per warp: slots b_first + wid, + NW, ...; each lane 32 of the item's 1024 values
         T acc[32];
 #pragma unroll

@@ -85,8 +85,8 @@ static Layout make_layout(long long p, long long n, int precision, int input_dty
     L.off_rowsum = take(P * 8);
     L.off_colsum = take(size_t(L.maxtiles) * kTJ * 8);
     // one partial-moment slot per (tile, CTA) segment; slot index tile + CTA, and a wave never
-    // uses more CTAs than it has (tile, chunk) units
-    const size_t units = size_t(L.maxtiles) * size_t(L.ld / chunk_of(precision));
+    // uses more CTAs than it has (tile, 32-sample group) units
+    const size_t units = size_t(L.maxtiles) * size_t(L.ld / kSub);
     // (the Gram's split partial tiles use the same region before the first iteration)
     const size_t pair_partials = (size_t(L.maxtiles) + std::min(size_t(kMaxGrid), units)) * kPairThreads * 16 * L.esz;
     L.off_partials =
