@@ -576,72 +576,46 @@ __device__ __forceinline__ void acc2_add(Acc2& s, float2 u) {
 template <class T>
 struct IterShared {
     int red[32];
-    int arrive[kStages];
-    int issued;
     int abort;
     int flag;
     double dred[32];
-    // the variables of the copy rows (tile rows, then the wave's columns) of the two
-    // most recent tiles a chunk was issued for, and how many of them are valid
-    int tvars[2][64 + kTJ];
-    int tvalid[2];
-    int ttag[2];
 };
 
 // ------------------------------------------------------------------ copy ring
-// Warp-cooperative: lane 0 posts the expected bytes, the lanes issue one 1-D bulk
-// copy per variable of the tile (rows then columns) for one chunk of samples.  The
-// variables of a tile are read from global memory once and kept in shared memory
-// (two tile slots): chunks are issued one warp at a time (the release chain orders
-// the issuing warps) and in increasing tile order within a wave.
+// Each warp copies its share of one chunk's rows (the tile's rows, then the wave's
+// columns): warp w the rows w SPW ... w SPW + SPW - 1, one 1-D bulk copy per row and
+// lane.  Every row is copied (a row without a variable copies row 0 of the data, which
+// no pair reads), so the stage always expects the same byte count, posted by warp 0.
+// The variables of the warp's rows are kept in registers (ctile, cvar) and read again
+// only when the tile changes (chunks are issued in increasing order within a wave).
 template <class T>
-__device__ __forceinline__ void issue_chunk(const Fit& f, IterShared<T>& sh, T* stage, uint64_t* bar,
-                                            long long unit, int nch, int nrow, int ncol) {
+__device__ __forceinline__ void issue_part(const Fit& f, T* stage, uint64_t* bar, long long unit, int nch, int nrow,
+                                           int ncol, int& ctile, int& cvar) {
     using Cfg = PairCfg<T>;
-    constexpr int CH = Cfg::CH, LDS = Cfg::LDS, TI = Cfg::TI;
-    constexpr int SLOTS = (TI + kTJ + 31) / 32;
-    static_assert(TI + kTJ <= 64 + kTJ, "tile variable cache too small");
-    const int lane = threadIdx.x & 31;
+    constexpr int CH = Cfg::CH, LDS = Cfg::LDS, TI = Cfg::TI, NW = Cfg::CONS / 32;
+    constexpr int SPW = (TI + kTJ) / NW;
+    static_assert(SPW * NW == TI + kTJ && SPW <= 32, "copy rows must split evenly over the warps");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int t = int(unit / nch), c = int(unit % nch);
-    const int cs = t & 1;
-    const T* xt = static_cast<const T*>(f.xt);
-    const size_t t0 = size_t(c) * CH;
-    volatile int* tag = sh.ttag;
-    if (__shfl_sync(0xffffffffu, tag[cs], 0) != t) {
-        int nv = 0;
-#pragma unroll
-        for (int k = 0; k < SLOTS; ++k) {
-            const int slot = lane + 32 * k;
-            int v = -1;
+    const int slot = w * SPW + lane;
+    if (t != ctile) {
+        ctile = t;
+        int v = -1;
+        if (lane < SPW) {
             if (slot < TI) {
                 const int row = t * TI + slot;
                 v = row < nrow ? ld2(f.rows + row) : -1;
-            } else if (slot < TI + kTJ) {
+            } else {
                 v = (slot - TI) < ncol ? ld2(f.cols + slot - TI) : -1;
             }
-            if (slot < TI + kTJ) sh.tvars[cs][slot] = v;
-            nv += __popc(__ballot_sync(0xffffffffu, v >= 0));
         }
-        if (lane == 0) sh.tvalid[cs] = nv;
-        __syncwarp();
-        if (lane == 0) tag[cs] = t;
-        __syncwarp();
+        cvar = v;
     }
-    int vars[SLOTS];
-#pragma unroll
-    for (int k = 0; k < SLOTS; ++k) {
-        const int slot = lane + 32 * k;
-        vars[k] = slot < TI + kTJ ? sh.tvars[cs][slot] : -1;
-    }
-    if (lane == 0) {
+    if (threadIdx.x == 0) mbar_expect_tx(bar, uint32_t(TI + kTJ) * CH * sizeof(T));
+    if (lane < SPW) {
         fence_proxy_async();
-        mbar_expect_tx(bar, uint32_t(sh.tvalid[cs]) * CH * sizeof(T));
-    }
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < SLOTS; ++k) {
-        const int slot = lane + 32 * k;
-        if (vars[k] >= 0) bulk_g2s(stage + slot * LDS, xt + size_t(vars[k]) * f.ld + t0, CH * sizeof(T), bar);
+        const T* xt = static_cast<const T*>(f.xt);
+        bulk_g2s(stage + slot * LDS, xt + size_t(cvar >= 0 ? cvar : 0) * f.ld + size_t(c) * CH, CH * sizeof(T), bar);
     }
 }
 
@@ -677,15 +651,12 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
     const unsigned long long tmo = ctl->timeout_ns;
     const int base = chunk_base;   // ring position of this wave's first chunk
 
-    if (tid < 32) {
-        if (lane < 2) sh.ttag[lane] = -1;   // the rows and columns changed with the wave
-        __syncwarp();
-        for (int k = 0; k < min(total, kStages); ++k) {
-            const int s = (base + k) % kStages;
-            issue_chunk<T>(f, sh, ring + size_t(s) * stage_elems<T>(), &full[s], c_lo + k, nch, nrow, ncol);
-        }
+    int ctile = -1, cvar = -1;   // this thread's copy row (rows and columns changed with the wave)
+    for (int k = 0; k < min(total, kStages); ++k) {
+        const int s = (base + k) % kStages;
+        issue_part<T>(f, ring + size_t(s) * stage_elems<T>(), &full[s], c_lo + k, nch, nrow, ncol, ctile, cvar);
     }
-    if (tid == 0) sh.issued = min(total, kStages);
+    int issued = min(total, kStages);   // chunks whose copies were issued
 
     const int ty = tid >> 4, tx = tid & 15;
     const int rsl[2] = {ty, ty + TI / 2}, csl[2] = {tx, tx + 16};
@@ -735,16 +706,14 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
             g = min(seg_end, (cg + 1) * GPC);
             const int pos = base + k;
             const int s = pos % kStages;
-            if (!mbar_wait_or_abort(&full[s], (pos / kStages) & 1, ctl, tmo, &sh.abort)) {
-                ok = false;
-                sh.abort = 1;
-                break;
-            }
+            const bool okw = mbar_wait_or_abort(&full[s], (pos / kStages) & 1, ctl, tmo, &sh.abort);
+            if (!okw) sh.abort = 1;
             const T* st = ring + size_t(s) * stage_elems<T>();
             const T* R0 = st + rsl[0] * LDS;
             const T* R1 = st + rsl[1] * LDS;
             const T* C0 = st + (TI + csl[0]) * LDS;
             const T* C1 = st + (TI + csl[1]) * LDS;
+            if (okw) {
             if constexpr (kF32) {
                 float2 s2[4], sr2[4];
 #pragma unroll
@@ -827,31 +796,24 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
                     }
                 }
             }
-            // release the stage; the last warp to release it refills it with the chunk
-            // kStages further on
-            __syncwarp();
-            int last = 0;
-            if (lane == 0) {
-                __threadfence_block();
-                last = atomicAdd(&sh.arrive[s], 1) == NW - 1;
-                if (last) {
-                    sh.arrive[s] = 0;
-                    __threadfence_block();
-                }
             }
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (last && k + kStages < total) {
-                const int s2i = (pos + kStages) % kStages;
-                issue_chunk<T>(f, sh, ring + size_t(s2i) * stage_elems<T>(), &full[s2i], c_lo + k + kStages, nch,
-                               nrow, ncol);
-                if (lane == 0) atomicMax(&sh.issued, k + kStages + 1);
+            // every warp is done with the stage (or a wait gave up: all leave together);
+            // each warp copies its rows of the chunk kStages further on into it
+            if (__syncthreads_or(!okw)) {
+                ok = false;
+                break;
+            }
+            if (k + kStages < total) {
+                issue_part<T>(f, ring + size_t(s) * stage_elems<T>(), &full[s], c_lo + k + kStages, nch, nrow, ncol,
+                              ctile, cvar);
+                issued = k + kStages + 1;
             }
         }
         if (__syncthreads_or(!ok)) {
             // A wait gave up (status recorded).  Give the copies still in flight a bounded
             // chance to land before the CTA leaves.
             if (tid == 0)
-                for (int k2 = k; k2 < sh.issued; ++k2) {
+                for (int k2 = k; k2 < issued; ++k2) {
                     const int pos = base + k2;
                     const unsigned long long t0 = global_ns();
                     while (!mbar_try_wait(&full[pos % kStages], (pos / kStages) & 1) &&
@@ -1141,10 +1103,7 @@ __global__ void __launch_bounds__(PairCfg<T>::CONS, 1) k_iteration(Fit f, int it
     if (vc->status != 0) return;
     const unsigned long long tmo = vc->timeout_ns;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 1);
-            sh.arrive[s] = 0;
-        }
+        for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
         sh.abort = 0;
         fence_barrier_init();
     }
