@@ -34,6 +34,11 @@ L2_FLUSH_BYTES = 256 << 20
 # Pair kernel SFU roofline: per pair-sample 4 ex2 (32 per SM per clock on sm_103a)
 # plus 2 lg2 per 32 samples (16 per SM per clock).
 SFU_CLK_PER_PAIR_SAMPLE = 4.0 / 32.0 + (2.0 / 32.0) / 16.0
+# DRAM bytes (read + write) per launch of the iteration kernel, from one ncu capture
+# of iterations 2 and 3 of a p = 1000, n = 1e4 fit (cold caches: the 40 MB of
+# normalised rows and the 8 MB covariance read once).  Valid for this kernel
+# version only: set to None when the kernel changes, until it is captured again.
+ITER_TRAFFIC_BYTES = 48.82e6 + 4.06e6
 
 
 def unpruned_pair_samples(p: int, n: int) -> float:
@@ -258,9 +263,11 @@ def run_ours(args, rank: int, world: int):
     nsm = props.multi_processor_count
     peak = nsm * (1.0 / SFU_CLK_PER_PAIR_SAMPLE) * sm_max * 1e6
     achieved = float(np.sum(pairs)) * n / (float(np.sum(pair_ms)) / 1000.0)
+    traffic = ITER_TRAFFIC_BYTES if (p, n) == (P_DEFAULT, N_DEFAULT) else None
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-samples/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "k_pair_wave<float>",
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_basis": "ncu dram__bytes_read+write of one launch (iteration 2 of a fit, cold caches)",
+                "kernel": "k_iteration<float>",
                 "peak_basis": f"SFU: 4 ex2 + 1/16 lg2 per pair-sample, {nsm} SMs x 32 ex2/clk at sm_max {sm_max:.0f} MHz"}
 
     line = {"metric": "pair-sample evals/s (unpruned-equivalent) at p=1000, n=1e4, mixed path",

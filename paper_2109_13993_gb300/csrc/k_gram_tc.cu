@@ -344,8 +344,8 @@ __global__ void k_gram_tc_reduce(Fit f, const float2* __restrict__ partial, cons
 }
 
 // ------------------------------------------------------------------ host side
-// Split of the sample axis: enough CTAs for one wave over the 152 SMs when the
-// triangle has few tiles, at most 32 splits, every split at least one k-step.
+// Split of the sample axis: as many splits as fit the triangle's tiles into one
+// wave over the 152 SMs (one CTA per SM), at most 32, every split at least one k-step.
 struct GramTcPlan {
     int nt, ntri, kb_total, kb_per_split, nsplit;
 };
@@ -354,7 +354,7 @@ static GramTcPlan gram_tc_plan(long long p, int ld) {
     g.nt = int((p + kGM - 1) / kGM);
     g.ntri = g.nt * (g.nt + 1) / 2;
     g.kb_total = ld / kGKB;
-    int want = (152 + g.ntri - 1) / g.ntri;
+    int want = 152 / g.ntri;
     want = want < 1 ? 1 : (want > 32 ? 32 : want);
     if (want > g.kb_total) want = g.kb_total;
     g.kb_per_split = (g.kb_total + want - 1) / want;
