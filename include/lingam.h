@@ -23,7 +23,9 @@
  *   - Errors are returned as lingam_status codes; nothing is thrown across
  *     the ABI.  Outputs are written only when the call returns LINGAM_OK.
  *   - The caller owns every buffer, the workspace included.  The library
- *     allocates no memory and keeps no state between calls.
+ *     allocates no memory.  The only state kept between calls is the
+ *     pair-tile autotuner's table (lingam_autotune) and the address of the
+ *     static scratch area (lingam_fit_static).
  *   - Data pointers may point to host or device memory; the library tells
  *     them apart with cudaPointerGetAttributes.  Host buffers are copied
  *     inside the call.  All device work runs on opts->stream and the call
@@ -59,7 +61,9 @@ typedef struct {
     int input_dtype;         /* element type of X: LINGAM_F32 or LINGAM_F64 */
     int prune;               /* 1 = threshold pruning (Sec. III-B), 0 = compare every pair */
     int reuse;               /* 1 = one evaluation per unordered pair (Sec. III-A), 0 = every ordered pair */
-    int tile_i, tile_j;      /* pair-tile shape override; 0 = autotuned */
+    int tile_i;              /* pair-tile rows of the mixed path: 32 or 64; 0 = lingam_tile_rows(p, n)
+                                (the autotuner's table); ignored by the FP64 path (32 rows) */
+    int tile_j;              /* reserved, must be 0 or 32 (tiles have 32 columns) */
     int split_n;             /* sample-axis split override; 0 = autotuned */
     double timeout_s;        /* bound on any device-side wait; <= 0 means 10 s */
     void* stream;            /* cudaStream_t to run on; NULL = the legacy default stream */
@@ -133,6 +137,28 @@ int lingam_fit(const void* X, long long p, long long n, int* order, double* B, v
  */
 int lingam_covariance(const void* X, long long p, long long n, double* Sigma, void* workspace,
                       const lingam_opts* opts, lingam_report* report);
+
+/*
+ * Pair-tile autotuner (the paper has no counterpart: its GPU design has one tile shape).
+ * The mixed path evaluates pairs in tiles of 64 or 32 rows (variables) by 32 columns;
+ * which is faster depends on how many variables remain and on n.  The library keeps a
+ * process-wide table of the choice per size bucket (ceil(log2 p), ceil(log2 n)); a
+ * bucket never measured uses 64-row tiles.
+ *
+ * lingam_tile_rows   -- the tile rows lingam_fit uses for a p x n problem when
+ *                       opts->tile_i is 0 (opts->tile_i = 32 or 64 forces a shape).
+ * lingam_autotune    -- measures the ordering of X (as lingam_fit with opts, B not
+ *                       fitted) once with each tile shape, records the faster one for
+ *                       X's size bucket and returns it in *tile_rows; ms[0], ms[1] (if
+ *                       ms is not NULL) receive the ordering times with 64 and 32 rows.
+ *                       Costs two fits; the workspace is as for lingam_fit.
+ * lingam_autotune_reset -- forgets every measured choice.
+ * The table is shared by all threads of the process (guarded by a mutex).
+ */
+int lingam_tile_rows(long long p, long long n);
+int lingam_autotune(const void* X, long long p, long long n, void* workspace, const lingam_opts* opts,
+                    int* tile_rows, double* ms);
+void lingam_autotune_reset(void);
 
 /* Workspace for lingam_fit_batch over `count` datasets of sizes p[k] x n[k]. */
 size_t lingam_workspace_size_batch(int count, const long long* p, const long long* n, const lingam_opts* opts);

@@ -25,7 +25,6 @@ constexpr int kTI = 32;
 constexpr int kTJ = 32;
 constexpr int kPairThreads = 512;
 // Rows of a pair tile for a precision (64 for the FP32 path, 32 for FP64).
-__host__ __device__ __forceinline__ int pair_tile_rows(int precision) { return precision == LINGAM_MIXED ? 64 : 32; }
 constexpr int kChunk = 128;            // samples per shared-memory stage (FP32 path)
 constexpr int kChunk64 = 64;           // samples per stage (FP64 path)
 constexpr int kSub = 32;               // samples per product group (one lg2 per group)
@@ -112,6 +111,7 @@ struct Fit {
     double* bout;        // [p x p] B (original indices)
     Ctl* ctl;
     int maxtiles;        // row tiles of a wave at most (ceil(p / kTI))
+    int tile_rows;       // rows of a pair tile: 64 or 32 (mixed path), 32 (FP64 path)
     int maxsplit;        // sample splits at most
 };
 

@@ -59,38 +59,38 @@
 
 namespace lingam {
 
-// Tile geometry per precision: TI rows x kTJ columns, CONS threads of 2 x 2
-// pairs each (rows ty and ty + TI/2, columns tx and tx + 16), one CTA per SM.
-template <class T>
-struct PairCfg;
-template <>
-struct PairCfg<float> {
-    static constexpr int TI = 64;
-    static constexpr int CONS = 512;
-    static constexpr int CH = kChunk;
-    static constexpr int LDS = kChunk + 4;    // padded smem row: conflict-free 16-byte loads
+// Pair-tile shapes: TI rows x kTJ columns, CONS threads of 2 x 2 pairs each (rows ty
+// and ty + TI/2, columns tx and tx + 16), sample chunks of CH staged in shared-memory
+// rows of LDS elements (padded: conflict-free 16-byte loads).  The FP32 path has two
+// shapes, chosen by the tile autotuner: 64-row tiles of 512 threads (one CTA per SM)
+// and 32-row tiles of 256 threads (two CTAs per SM, less padding waste when few
+// variables remain).
+template <class T_, int TI_, int CONS_, int CH_, int LDS_, int MINB_>
+struct PairShape {
+    using T = T_;
+    static constexpr int TI = TI_;
+    static constexpr int CONS = CONS_;
+    static constexpr int CH = CH_;
+    static constexpr int LDS = LDS_;
+    static constexpr int MINB = MINB_;   // CTAs per SM the launch bounds ask for
 };
-template <>
-struct PairCfg<double> {
-    static constexpr int TI = 32;
-    static constexpr int CONS = 256;
-    static constexpr int CH = kChunk64;
-    static constexpr int LDS = kChunk64 + 2;  // padded smem row
-};
+using CfgF64 = PairShape<float, 64, 512, kChunk, kChunk + 4, 1>;      // FP32, 64-row tiles
+using CfgF32 = PairShape<float, 32, 256, kChunk, kChunk + 4, 2>;      // FP32, 32-row tiles
+using CfgD = PairShape<double, 32, 256, kChunk64, kChunk64 + 2, 1>;   // FP64 path
 
 constexpr int kSortMax = 8192;   // candidate sort in shared memory up to this many variables
 
-template <class T>
+template <class Cfg>
 __host__ __device__ constexpr size_t stage_elems() {
-    return size_t(PairCfg<T>::TI + kTJ) * PairCfg<T>::LDS;
+    return size_t(Cfg::TI + kTJ) * Cfg::LDS;
 }
-template <class T>
+template <class Cfg>
 __host__ __device__ constexpr size_t ring_bytes() {
-    return size_t(kStages) * stage_elems<T>() * sizeof(T);
+    return size_t(kStages) * stage_elems<Cfg>() * sizeof(typename Cfg::T);
 }
-template <class T>
+template <class Cfg>
 size_t iter_smem_bytes() {
-    const size_t ring = ring_bytes<T>();
+    const size_t ring = ring_bytes<Cfg>();
     const size_t sort = size_t(kSortMax) * sizeof(unsigned long long);
     return (ring > sort ? ring : sort) + kStages * sizeof(uint64_t);
 }
@@ -270,7 +270,7 @@ __device__ __forceinline__ int cta_of_unit(long long v, long long U, long long G
 }
 
 // ------------------------------------------------------------------ plan (CTA 0)
-template <int NTH>
+template <int NTH, int TI>
 __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* smem, int* red) {
     Ctl* ctl = f.ctl;
     const int p = f.p, tid = threadIdx.x;
@@ -376,8 +376,7 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
             for (int c = 0; c < nc; ++c) f.cols[c] = f.sigma[c];
             ctl->ncol = nc;
             ctl->nrow = r;
-            const int ti = pair_tile_rows(f.precision);
-            ctl->ntiles = (r + ti - 1) / ti;
+            ctl->ntiles = (r + TI - 1) / TI;
         }
     }
 }
@@ -573,7 +572,6 @@ __device__ __forceinline__ void acc2_add(Acc2& s, float2 u) {
 }
 
 // Shared state of one CTA (besides the dynamic copy ring).
-template <class T>
 struct IterShared {
     int red[32];
     int abort;
@@ -588,10 +586,10 @@ struct IterShared {
 // no pair reads), so the stage always expects the same byte count, posted by warp 0.
 // The variables of the warp's rows are kept in registers (ctile, cvar) and read again
 // only when the tile changes (chunks are issued in increasing order within a wave).
-template <class T>
-__device__ __forceinline__ void issue_part(const Fit& f, T* stage, uint64_t* bar, long long unit, int nch, int nrow,
+template <class Cfg>
+__device__ __forceinline__ void issue_part(const Fit& f, typename Cfg::T* stage, uint64_t* bar, long long unit, int nch, int nrow,
                                            int ncol, int& ctile, int& cvar) {
-    using Cfg = PairCfg<T>;
+    using T = typename Cfg::T;
     constexpr int CH = Cfg::CH, LDS = Cfg::LDS, TI = Cfg::TI, NW = Cfg::CONS / 32;
     constexpr int SPW = (TI + kTJ) / NW;
     static_assert(SPW * NW == TI + kTJ && SPW <= 32, "copy rows must split evenly over the warps");
@@ -625,10 +623,10 @@ struct Wave {
     int ntiles, ncol, nrow;
 };
 
-template <class T>
-__device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring, uint64_t* full, IterShared<T>& sh,
+template <class Cfg>
+__device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, typename Cfg::T* ring, uint64_t* full, IterShared& sh,
                               int& chunk_base) {
-    using Cfg = PairCfg<T>;
+    using T = typename Cfg::T;
     constexpr int CH = Cfg::CH, LDS = Cfg::LDS, TI = Cfg::TI, CONS = Cfg::CONS;
     constexpr int NW = CONS / 32;
     constexpr bool kF32 = std::is_same<T, float>::value;
@@ -654,7 +652,7 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
     int ctile = -1, cvar = -1;   // this thread's copy row (rows and columns changed with the wave)
     for (int k = 0; k < min(total, kStages); ++k) {
         const int s = (base + k) % kStages;
-        issue_part<T>(f, ring + size_t(s) * stage_elems<T>(), &full[s], c_lo + k, nch, nrow, ncol, ctile, cvar);
+        issue_part<Cfg>(f, ring + size_t(s) * stage_elems<Cfg>(), &full[s], c_lo + k, nch, nrow, ncol, ctile, cvar);
     }
     int issued = min(total, kStages);   // chunks whose copies were issued
 
@@ -708,7 +706,7 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
             const int s = pos % kStages;
             const bool okw = mbar_wait_or_abort(&full[s], (pos / kStages) & 1, ctl, tmo, &sh.abort);
             if (!okw) sh.abort = 1;
-            const T* st = ring + size_t(s) * stage_elems<T>();
+            const T* st = ring + size_t(s) * stage_elems<Cfg>();
             const T* R0 = st + rsl[0] * LDS;
             const T* R1 = st + rsl[1] * LDS;
             const T* C0 = st + (TI + csl[0]) * LDS;
@@ -804,7 +802,7 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
                 break;
             }
             if (k + kStages < total) {
-                issue_part<T>(f, ring + size_t(s) * stage_elems<T>(), &full[s], c_lo + k + kStages, nch, nrow, ncol,
+                issue_part<Cfg>(f, ring + size_t(s) * stage_elems<Cfg>(), &full[s], c_lo + k + kStages, nch, nrow, ncol,
                               ctile, cvar);
                 issued = k + kStages + 1;
             }
@@ -847,9 +845,10 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, T* ring
 // tile's I buffer; the item that completes a tile reduces its rows and columns
 // (squared contributions summed in FP64), and the item that completes the wave's
 // last tile runs the wave finalisation.
-template <class T>
-__device__ __noinline__ void merge_phase(const Fit& f, const Wave& wv, int it, IterShared<T>& sh, T* scratch) {
-    using Cfg = PairCfg<T>;
+template <class Cfg>
+__device__ __noinline__ void merge_phase(const Fit& f, const Wave& wv, int it, IterShared& sh,
+                                         typename Cfg::T* scratch) {
+    using T = typename Cfg::T;
     constexpr int CH = Cfg::CH, TI = Cfg::TI, CONS = Cfg::CONS;
     constexpr int NW = CONS / 32;
     constexpr int PARTS = CONS / 64;            // items per tile
@@ -978,9 +977,10 @@ __device__ __noinline__ void merge_phase(const Fit& f, const Wave& wv, int it, I
 
 // ------------------------------------------------------------------ removal phases
 // UpdateData (Algorithm 7) with the new H(x_w) terms; rows of U spread over the CTAs.
-template <class T>
-__device__ __noinline__ void remove_data_phase(const Fit& f, IterShared<T>& sh) {
-    constexpr int NTH = PairCfg<T>::CONS;
+template <class Cfg>
+__device__ __noinline__ void remove_data_phase(const Fit& f, IterShared& sh) {
+    using T = typename Cfg::T;
+    constexpr int NTH = Cfg::CONS;
     Ctl* ctl = f.ctl;
     volatile Ctl* vc = ctl;
     const int r = vc->r, root = vc->root, p = f.p, ld = f.ld, tid = threadIdx.x;
@@ -1068,9 +1068,9 @@ __device__ __noinline__ void remove_data_phase(const Fit& f, IterShared<T>& sh) 
 // w, j in U without the root; rows spread over the CTAs, columns in index order.
 // Sigma is symmetric, so Sigma[j,root] is read from the root's row (contiguous).
 // The root's row and column are only read, so the update is done in place.
-template <class T>
+template <class Cfg>
 __device__ __noinline__ void remove_cov_phase(const Fit& f) {
-    constexpr int NTH = PairCfg<T>::CONS;
+    constexpr int NTH = Cfg::CONS;
     volatile Ctl* vc = f.ctl;
     const int r = vc->r, root = vc->root, p = f.p, tid = threadIdx.x;
     const double* rootrow = f.sig + size_t(root) * p;
@@ -1088,14 +1088,14 @@ __device__ __noinline__ void remove_cov_phase(const Fit& f) {
 }
 
 // ------------------------------------------------------------------ the iteration kernel
-template <class T>
-__global__ void __launch_bounds__(PairCfg<T>::CONS, 1) k_iteration(Fit f, int it) {
+template <class Cfg>
+__global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int it) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ IterShared<T> sh;
-    using Cfg = PairCfg<T>;
+    __shared__ IterShared sh;
+    using T = typename Cfg::T;
     Ctl* ctl = f.ctl;
     T* ring = reinterpret_cast<T*>(smem_raw);
-    const size_t ring_or_sort = ring_bytes<T>() > size_t(kSortMax) * 8 ? ring_bytes<T>() : size_t(kSortMax) * 8;
+    const size_t ring_or_sort = ring_bytes<Cfg>() > size_t(kSortMax) * 8 ? ring_bytes<Cfg>() : size_t(kSortMax) * 8;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + ring_or_sort);
     volatile Ctl* vc = ctl;
     // A failure recorded before this launch: every CTA reads it before the first
@@ -1109,56 +1109,58 @@ __global__ void __launch_bounds__(PairCfg<T>::CONS, 1) k_iteration(Fit f, int it
     }
     __syncthreads();
 
-    if (blockIdx.x == 0) plan_phase<Cfg::CONS>(f, it, smem_raw, sh.red);
+    if (blockIdx.x == 0) plan_phase<Cfg::CONS, Cfg::TI>(f, it, smem_raw, sh.red);
     if (!grid_sync(ctl, tmo)) return;
     int chunk_base = 0;
     while (!vc->done) {
         const Wave wv = {vc->ntiles, vc->ncol, vc->nrow};
-        if (!compute_phase<T>(f, wv, ring, full, sh, chunk_base)) {
+        if (!compute_phase<Cfg>(f, wv, ring, full, sh, chunk_base)) {
             ctl->abort = 1;
             return;
         }
         if (!grid_sync(ctl, tmo)) return;
-        merge_phase<T>(f, wv, it, sh, ring);
+        merge_phase<Cfg>(f, wv, it, sh, ring);
         fence_proxy_async();   // the merge used the copy ring as scratch
         if (!grid_sync(ctl, tmo)) return;
     }
     if (it < f.p - 1 && vc->root >= 0) {
-        remove_data_phase<T>(f, sh);
+        remove_data_phase<Cfg>(f, sh);
         if (!grid_sync(ctl, tmo)) return;
-        remove_cov_phase<T>(f);
+        remove_cov_phase<Cfg>(f);
     }
 }
 
 // ------------------------------------------------------------------ host side
-template <class T>
+template <class Cfg>
 static int grid_for(int nsm) {
     int per_sm = 0;
-    const size_t smem = iter_smem_bytes<T>();
-    if (ensure_smem_attr(reinterpret_cast<const void*>(k_iteration<T>), smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iteration<T>, PairCfg<T>::CONS, smem) !=
-        cudaSuccess)
+    const size_t smem = iter_smem_bytes<Cfg>();
+    if (ensure_smem_attr(reinterpret_cast<const void*>(k_iteration<Cfg>), smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iteration<Cfg>, Cfg::CONS, smem) != cudaSuccess)
         return 0;
-    return per_sm >= 1 ? nsm : 0;   // one CTA per SM
+    if (per_sm < 1) return 0;
+    return nsm * (per_sm < Cfg::MINB ? per_sm : Cfg::MINB);   // all CTAs co-resident
 }
 
 int iteration_grid(const Fit& f, int nsm) {
-    return f.precision == LINGAM_MIXED ? grid_for<float>(nsm) : grid_for<double>(nsm);
+    if (f.precision != LINGAM_MIXED) return grid_for<CfgD>(nsm);
+    return f.tile_rows == 32 ? grid_for<CfgF32>(nsm) : grid_for<CfgF64>(nsm);
 }
 
-template <class T>
+template <class Cfg>
 static cudaError_t launch_iter(const Fit& f, int it, int grid, cudaStream_t st) {
-    const size_t smem = iter_smem_bytes<T>();
-    cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(k_iteration<T>), smem);
+    const size_t smem = iter_smem_bytes<Cfg>();
+    cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(k_iteration<Cfg>), smem);
     if (e != cudaSuccess) return e;
     Fit fc = f;
     void* args[] = {&fc, &it};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_iteration<T>), dim3(grid),
-                                       dim3(PairCfg<T>::CONS), args, smem, st);
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_iteration<Cfg>), dim3(grid), dim3(Cfg::CONS),
+                                       args, smem, st);
 }
 
 cudaError_t launch_iteration(const Fit& f, int it, int grid, cudaStream_t st) {
-    return f.precision == LINGAM_MIXED ? launch_iter<float>(f, it, grid, st) : launch_iter<double>(f, it, grid, st);
+    if (f.precision != LINGAM_MIXED) return launch_iter<CfgD>(f, it, grid, st);
+    return f.tile_rows == 32 ? launch_iter<CfgF32>(f, it, grid, st) : launch_iter<CfgF64>(f, it, grid, st);
 }
 
 }  // namespace lingam

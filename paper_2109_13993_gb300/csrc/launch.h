@@ -32,4 +32,10 @@ int iteration_grid(const Fit& f, int nsm);
 // B from the order: Cholesky of the covariance in causal order, B = I - diag(R) R^{-1}.
 cudaError_t launch_fit_B(const Fit& f, cudaStream_t st);
 
+// Pair-tile autotuner (autotune.cu): the tile rows of the mixed path for a problem size,
+// recording a measured choice, and forgetting all of them.
+int autotune_tile_rows(long long p, long long n);
+void autotune_record(long long p, long long n, int tile_rows);
+void autotune_clear();
+
 }  // namespace lingam

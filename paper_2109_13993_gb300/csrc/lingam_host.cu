@@ -106,10 +106,18 @@ static Layout make_layout(long long p, long long n, int precision, int input_dty
     return L;
 }
 
+// Pair-tile rows of the mixed path: the caller's choice (32 or 64), else the tile
+// autotuner's choice for this problem size.
+static int choose_tile_rows(int p, int n, int tile_i) {
+    if (tile_i == 32 || tile_i == 64) return tile_i;
+    return autotune_tile_rows(p, n);
+}
+
 static bool valid_opts(const lingam_opts& o) {
     return (o.precision == LINGAM_MIXED || o.precision == LINGAM_FP64) &&
            (o.input_dtype == LINGAM_F32 || o.input_dtype == LINGAM_F64) && (o.prune == 0 || o.prune == 1) &&
-           (o.reuse == 0 || o.reuse == 1) && o.split_n >= 0 && o.tile_i >= 0 && o.tile_j >= 0;
+           (o.reuse == 0 || o.reuse == 1) && o.split_n >= 0 && (o.tile_i == 0 || o.tile_i == 32 || o.tile_i == 64) &&
+           (o.tile_j == 0 || o.tile_j == 32);
 }
 
 static bool is_device_ptr(const void* ptr) {
@@ -186,6 +194,7 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
     f.ctl = reinterpret_cast<Ctl*>(base + L.off_ctl);
     f.maxtiles = L.maxtiles;
     f.maxsplit = L.maxsplit;
+    f.tile_rows = o.precision == LINGAM_MIXED ? choose_tile_rows(p, n, o.tile_i) : 32;
 
 #define CK(call)                                  \
     do {                                          \
@@ -370,6 +379,42 @@ int lingam_covariance(const void* X, long long p, long long n, double* Sigma, vo
     if (!Sigma || o.forced_order) return LINGAM_EINVAL;
     return fit_one(X, p, n, nullptr, nullptr, workspace, o, report, Sigma);
 }
+
+int lingam_tile_rows(long long p, long long n) {
+    if (p < 1 || n < 3) return 0;
+    return autotune_tile_rows(p, n);
+}
+
+int lingam_autotune(const void* X, long long p, long long n, void* workspace, const lingam_opts* opts,
+                    int* tile_rows, double* ms) {
+    lingam_opts o;
+    lingam_default_opts(&o);
+    if (opts) o = *opts;
+    if (!tile_rows || o.precision != LINGAM_MIXED || o.forced_order) return LINGAM_EINVAL;
+    if (p < 1 || n < 3 || p > kMaxP) return LINGAM_EINVAL;
+    std::vector<int> order(static_cast<size_t>(p));
+    const int cand[2] = {64, 32};
+    double t[2] = {0.0, 0.0};
+    for (int c = 0; c < 2; ++c) {
+        lingam_opts oc = o;
+        oc.tile_i = cand[c];
+        lingam_report rep;
+        std::memset(&rep, 0, sizeof(rep));
+        const int st = fit_one(X, p, n, order.data(), nullptr, workspace, oc, &rep);
+        if (st != LINGAM_OK) return st;
+        t[c] = rep.t_order_ms;
+    }
+    const int best = t[1] < t[0] ? 32 : 64;
+    autotune_record(p, n, best);
+    *tile_rows = best;
+    if (ms) {
+        ms[0] = t[0];
+        ms[1] = t[1];
+    }
+    return LINGAM_OK;
+}
+
+void lingam_autotune_reset(void) { autotune_clear(); }
 
 size_t lingam_workspace_size_batch(int count, const long long* p, const long long* n, const lingam_opts* opts) {
     if (count < 0 || (count > 0 && (!p || !n))) return 0;

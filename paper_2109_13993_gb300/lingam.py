@@ -82,6 +82,13 @@ def load():
     L.lingam_covariance.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.POINTER(Report)]
     L.lingam_covariance.restype = ctypes.c_int
+    L.lingam_tile_rows.argtypes = [ctypes.c_longlong, ctypes.c_longlong]
+    L.lingam_tile_rows.restype = ctypes.c_int
+    L.lingam_autotune.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p,
+                                  ctypes.POINTER(Opts), _c_int_p, _c_dbl_p]
+    L.lingam_autotune.restype = ctypes.c_int
+    L.lingam_autotune_reset.argtypes = []
+    L.lingam_autotune_reset.restype = None
     L.lingam_status_string.argtypes = [ctypes.c_int]
     L.lingam_status_string.restype = ctypes.c_char_p
     _lib = L
@@ -100,7 +107,7 @@ def status_string(status: int) -> str:
 
 def make_opts(precision: str = "mixed", input_dtype=np.float32, prune: bool = True, reuse: bool = True,
               split_n: int = 0, timeout_s: float = 10.0, stream=None, forced_order=None, max_iters: int = 0,
-              timing: bool = False) -> tuple[Opts, object]:
+              timing: bool = False, tile_i: int = 0) -> tuple[Opts, object]:
     o = Opts()
     load().lingam_default_opts(ctypes.byref(o))
     o.precision = {"mixed": LINGAM_MIXED, "fp64": LINGAM_FP64}[precision]
@@ -112,6 +119,7 @@ def make_opts(precision: str = "mixed", input_dtype=np.float32, prune: bool = Tr
     o.stream = ctypes.c_void_p(stream) if stream else None
     o.max_iters = int(max_iters)
     o.timing = int(bool(timing))
+    o.tile_i = int(tile_i)
     keep = None
     if forced_order is not None:
         keep = np.ascontiguousarray(forced_order, dtype=np.int32)
@@ -174,7 +182,8 @@ def _data_ptr(X):
 
 def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, forced_order=None,
         want_scores: bool = False, want_B: bool = True, split_n: int = 0, timeout_s: float = 10.0,
-        stream=None, workspace=None, max_iters: int = 0, timing: bool = False, out=None) -> FitResult:
+        stream=None, workspace=None, max_iters: int = 0, timing: bool = False, out=None,
+        tile_i: int = 0) -> FitResult:
     """lingam_fit on X (p x n, numpy on the host or a torch tensor on the GPU)."""
     L = load()
     ptr, p, n, dt, keep = _data_ptr(X)
@@ -182,7 +191,7 @@ def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, for
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     o, keep_forced = make_opts(precision, dt, prune, reuse, split_n, timeout_s, stream, forced_order, max_iters,
-                               timing)
+                               timing, tile_i)
     need = int(L.lingam_workspace_size(p, n, ctypes.byref(o)))
     if need == 0:
         raise LingamError(LINGAM_EINVAL, "invalid sizes or options")
@@ -242,6 +251,36 @@ def covariance(X, precision: str = "mixed", stream=None, workspace=None, out=Non
         raise LingamError(st, status_string(st))
     return S, {"standardize": rep.t_standardize_ms, "gram": rep.t_gram_ms,
                "kernel_launches": int(rep.kernel_launches)}
+
+
+def tile_rows(p: int, n: int) -> int:
+    """Tile rows the mixed path uses for a p x n problem (the autotuner's table)."""
+    return int(load().lingam_tile_rows(p, n))
+
+
+def autotune(X, stream=None, workspace=None):
+    """lingam_autotune on X: times the ordering with 64- and 32-row pair tiles, records
+    the faster for X's size bucket; returns (tile_rows, {64: ms, 32: ms})."""
+    L = load()
+    ptr, p, n, dt, keep = _data_ptr(X)
+    if stream is None:
+        stream = _torch().cuda.current_stream().cuda_stream
+    o, _ = make_opts("mixed", dt, stream=stream)
+    need = int(L.lingam_workspace_size(p, n, ctypes.byref(o)))
+    if workspace is None or workspace.numel() < need:
+        workspace = alloc_workspace(need)
+    tr = ctypes.c_int(0)
+    ms = (ctypes.c_double * 2)()
+    st = L.lingam_autotune(ctypes.c_void_p(ptr), p, n, ctypes.c_void_p(workspace.data_ptr()), ctypes.byref(o),
+                           ctypes.byref(tr), ms)
+    del keep
+    if st != LINGAM_OK:
+        raise LingamError(st, status_string(st))
+    return int(tr.value), {64: float(ms[0]), 32: float(ms[1])}
+
+
+def autotune_reset():
+    load().lingam_autotune_reset()
 
 
 def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = True, stream=None):

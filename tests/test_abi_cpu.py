@@ -60,3 +60,15 @@ def test_fit_rejects_bad_arguments_without_gpu_work(lib):
     order = np.zeros(3, dtype=np.int32)
     assert lib.lingam_fit(ctypes.c_void_p(x.ctypes.data), 3, 2, order.ctypes.data, None, None, None,
                           None) == lingam.LINGAM_EINVAL
+
+
+def test_tile_rows_default_rule(lib):
+    # the autotuner's default before any measurement: 64-row tiles
+    lingam.autotune_reset()
+    assert lingam.tile_rows(20, 2000) == 64
+    assert lingam.tile_rows(1000, 10000) == 64
+    assert lingam.tile_rows(0, 100) == 0
+    o, _ = lingam.make_opts()
+    for bad in (16, 48, 128):
+        o.tile_i = bad
+        assert lib.lingam_workspace_size(10, 100, ctypes.byref(o)) == 0

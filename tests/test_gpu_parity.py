@@ -68,6 +68,40 @@ def _check_argmin_resolved(gpu_S, ora_S, tau_it):
     return resolved
 
 
+def _per_score_bound(gpu_S, ora_S, kappa_max):
+    """Per-score error bound of the mixed path.  S = sum_j min(0, I_j)^2 over m
+    partners, and an FP32 rounding dI (about 1e-6 absolute) of each I_j moves S by at
+    most 2 dI sqrt(m S) + m dI^2; the measured kappa = max (|dS| - m (2e-6)^2) / sqrt(m S)
+    must stay below kappa_max.  Returns tau[it, v] = kappa sqrt(m S) + m (2e-6)^2."""
+    m = np.maximum((~np.isnan(ora_S)).sum(axis=1, keepdims=True) - 1, 1)
+    Sm = np.where(np.isnan(ora_S), 0.0, ora_S)
+    root = np.sqrt(m * Sm)
+    floor = m * (2e-6) ** 2
+    err = np.abs(np.where(np.isnan(ora_S), 0.0, gpu_S - Sm))
+    excess = np.maximum(err - floor, 0.0)
+    assert np.all((excess == 0) | (root > 0)), "error above the floor on a zero score"
+    kappa = float(np.max(np.where(root > 0, excess / np.where(root > 0, root, 1.0), 0.0)))
+    assert kappa <= kappa_max, f"per-score error ratio {kappa:.2e} above {kappa_max:.0e}"
+    return kappa * root + floor, kappa
+
+
+def _check_argmin_resolved_per_score(gpu_S, ora_S, tau):
+    """Forced-order mode with per-score bounds: an iteration is resolved when the
+    oracle's second-lowest score exceeds the lowest by more than the two scores'
+    bounds; there the GPU's argmin must equal the oracle's."""
+    resolved = 0
+    for it in range(ora_S.shape[0]):
+        row = ora_S[it]
+        alive = np.nonzero(~np.isnan(row))[0]
+        if len(alive) < 2:
+            continue
+        o = alive[np.lexsort((alive, row[alive]))]
+        if row[o[1]] - row[o[0]] > tau[it, o[0]] + tau[it, o[1]]:
+            resolved += 1
+            assert _argmin(gpu_S[it]) == o[0], f"iteration {it}"
+    return resolved
+
+
 def _check_free_run(gpu_order, ora_order, ora_S, tau_it):
     """Free run: the orders agree until the first iteration where they differ,
     and that iteration must be one the oracle margin does not resolve."""
@@ -98,25 +132,34 @@ def test_fp64_path_matches_oracle(seed):
 
 # ---------------------------------------------------------------- mixed path vs oracle, 1e-4
 
-@pytest.mark.parametrize("name,seed", [("p20_n2000", 1), ("p20_n2000", 2), ("p100_n10000", 1)])
-def test_mixed_path_matches_oracle(name, seed):
+@pytest.mark.parametrize("name,seed,tile_i", [("p20_n2000", 1, 64), ("p20_n2000", 2, 32), ("p100_n10000", 1, 64),
+                                            ("p100_n10000", 1, 32)])
+def test_mixed_path_matches_oracle(name, seed, tile_i):
     d = synth.workload(name, seed=seed)
     X32 = d.X.astype(np.float32)
     o_order, o_B, o_S = oracle.fit(X32.astype(np.float64))
     res = lingam.fit(_dev(X32, torch.float32), precision="mixed", prune=False, forced_order=o_order,
-                     want_scores=True)
+                     want_scores=True, tile_i=tile_i)
     tau = _check_scores(res.scores, o_S, rtol=0.0, atol=1e-4)
     resolved = _check_argmin_resolved(res.scores, o_S, tau)
-    free = lingam.fit(_dev(X32, torch.float32), precision="mixed")
+    tau_v, kappa = _per_score_bound(res.scores, o_S, kappa_max=1e-5)
+    resolved_v = _check_argmin_resolved_per_score(res.scores, o_S, tau_v)
+    free = lingam.fit(_dev(X32, torch.float32), precision="mixed", tile_i=tile_i)
     upto = _check_free_run(free.order, o_order, o_S, tau)
-    print(f"{name}/{seed}: max score error {tau.max():.2e}; {resolved} of {len(o_order)} iterations "
-          f"margin-resolved; free-run order identical on the first {upto}")
+    print(f"{name}/{seed} tile {tile_i}: max score error {tau.max():.2e}; {resolved} of {len(o_order)} iterations "
+          f"resolved by the per-iteration bound, {resolved_v} by the per-score bound (kappa {kappa:.1e}); "
+          f"free-run order identical on the first {upto}")
     assert sorted(free.order.tolist()) == list(range(len(o_order)))
     scale = np.abs(o_B).max()
     assert np.abs(res.B - o_B).max() <= 1e-4 * max(1.0, scale)
 
 
 # ---------------------------------------------------------------- threshold pruning is exact
+
+def pr_tile(X):
+    """Tile rows the library picks for X by default (the autotuner's choice)."""
+    import ctypes
+    return lingam.tile_rows(X.shape[0], X.shape[1])
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_pruning_and_reuse_do_not_change_the_result(precision):
@@ -126,6 +169,13 @@ def test_pruning_and_reuse_do_not_change_the_result(precision):
     full = lingam.fit(X, precision=precision, prune=False)
     pr = lingam.fit(X, precision=precision, prune=True)
     assert np.array_equal(full.order, pr.order)
+    if precision == "mixed":
+        # the other tile shape groups each pair's samples differently: the same order, and
+        # scores equal up to the FP32 rounding of I (about 1e-6 absolute on Eq. HApp values
+        # near 1.4), which moves S = sum_j I_j^2 by at most 2e-6 sqrt(m S) <= 2e-8 here
+        other = lingam.fit(X, precision=precision, prune=True, tile_i=32 if pr_tile(X) == 64 else 64)
+        assert np.array_equal(other.order, pr.order)
+        assert np.allclose(other.root_score, pr.root_score, rtol=1e-4, atol=2e-8)
     # same scores up to the FP32 rounding of how a pair's samples were split across CTAs
     assert np.allclose(pr.root_score, full.root_score, rtol=1e-4, atol=1e-10)
     assert full.pairs_total == full.pairs_unpruned
@@ -234,3 +284,16 @@ def test_full_size_sampled_scores():
         err = np.abs(row[sample] - ora)
         assert err.max() <= 1e-4, (k, err.max())
         print(f"iteration {k}: {len(complete)} complete variables, max |dS| over {len(sample)} sampled = {err.max():.2e}")
+
+
+def test_autotuner_records_its_choice():
+    d = synth.workload("p100_n10000", seed=2)
+    X = _dev(d.X.astype(np.float32), torch.float32)
+    lingam.autotune_reset()
+    chosen, ms = lingam.autotune(X)
+    assert chosen in (32, 64) and ms[64] > 0 and ms[32] > 0
+    assert chosen == (32 if ms[32] < ms[64] else 64)
+    assert lingam.tile_rows(100, 10000) == chosen
+    print(f"autotune p=100 n=1e4: 64-row {ms[64]:.2f} ms, 32-row {ms[32]:.2f} ms -> {chosen}")
+    lingam.autotune_reset()
+    assert lingam.tile_rows(100, 10000) == 64
