@@ -164,15 +164,44 @@ void lingam_autotune_reset(void);
 size_t lingam_workspace_size_batch(int count, const long long* p, const long long* n, const lingam_opts* opts);
 
 /*
- * lingam_fit_batch -- `count` independent problems (for instance bootstrap
- * resamples).  X[k], order[k], B[k] as in lingam_fit for dataset k; B[k] may
- * be NULL.  status[k] (host array, may be NULL) receives each dataset's
- * status; report may be NULL or an array of `count` reports.  Returns the
- * first non-OK dataset status, else LINGAM_OK.
+ * lingam_fit_batch -- `count` independent problems of uneven p and n (Algorithm 3 on
+ * each; the paper fits one dataset at a time).  X[k], p[k], n[k], order[k], B[k] as in
+ * lingam_fit for dataset k; B may be NULL (no B for any dataset) and a B[k] may be
+ * NULL (no B for that one).  status[k] (host array, may be NULL) receives each
+ * dataset's status; report may be NULL or an array of `count` reports (their time
+ * fields are set to -1: the datasets run together).  Returns the first non-OK dataset
+ * status, else LINGAM_OK.  A dataset that turns out degenerate does not stop the
+ * others; a timeout stops all of them.
+ *
+ * All problems run in one persistent cooperative launch per 512 problems, in
+ * lockstep over iterations: each wave's pair tiles of all problems are partitioned
+ * over the whole GPU together.  The device work of a call is captured into a CUDA
+ * graph on the second call with the same workspace and problem shapes (and options),
+ * and replayed by every later such call; calls on the legacy default stream (NULL)
+ * run without a graph.  opts->forced_order must be NULL and opts->max_iters 0; the
+ * pair tiles have 64 rows (mixed) or 32 (FP64).
  */
 int lingam_fit_batch(int count, const void* const* X, const long long* p, const long long* n, int* const* order,
                      double* const* B, void* workspace, const lingam_opts* opts, int* status,
                      lingam_report* report);
+
+/* Workspace for lingam_fit_bootstrap of nboot resamples of a p x n dataset. */
+size_t lingam_workspace_size_bootstrap(long long p, long long n, int nboot, const lingam_opts* opts);
+
+/*
+ * lingam_fit_bootstrap -- nboot bootstrap resamples of one dataset, as lingam_fit_batch.
+ *   X       p x n row-major samples (opts->input_dtype), host or device, read in place
+ *           (copied once if on the host).
+ *   idx     nboot x n int indices in [0, n), host or device: resample b is the p x n
+ *           matrix whose column t is column idx[b n + t] of X (observations drawn with
+ *           replacement); the library draws no random numbers.
+ *   order   nboot x p ints, host or device: order[b p + k] as lingam_fit's order[k].
+ *   B       NULL or nboot x p x p doubles: resample b's B at B + b p p.
+ *   status, report as lingam_fit_batch (arrays of nboot).
+ * The gather of the resampled columns is fused into the normalisation of the rows.
+ */
+int lingam_fit_bootstrap(const void* X, long long p, long long n, int nboot, const int* idx, int* order, double* B,
+                         void* workspace, const lingam_opts* opts, int* status, lingam_report* report);
 
 /*
  * lingam_fit_static -- lingam_fit for callers that cannot allocate device memory.

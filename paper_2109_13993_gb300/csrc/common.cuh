@@ -70,6 +70,15 @@ struct Ctl {
 };
 
 // Device pointers of one fit, carved out of the caller's workspace.
+// Where a batch problem's samples come from: row i of the problem is the row of
+// x with stride ld (elements of the input type), sample t at column t, or at
+// column idx[t] for a bootstrap resample.
+struct SrcDesc {
+    const void* x;
+    const int* idx;
+    long long ld;
+};
+
 struct Fit {
     int p;               // variables
     int n;               // samples

@@ -65,6 +65,78 @@ __global__ void k_B_out(Fit f) {
     f.bout[size_t(f.order[a]) * p + f.order[b]] = v;
 }
 
+// The same fit for a problem of p <= kBSmall in one CTA (batches: one CTA per
+// problem): C in shared memory, Cholesky C = L L^T in place (L lower, L = R), then
+// thread b solves column b of L^{-1} by forward substitution into the problem's rinv
+// (column-major, scratch) and writes B[K[a]][K[b]] = -L[a][a] Linv[a][b] for a > b.
+// Problems with p > kBSmall, or whose status is bad, are left to other launches.
+constexpr int kBSmall = 128;
+constexpr int kBThreads = 256;
+
+__global__ void __launch_bounds__(kBThreads) k_bfit_small(const Fit* __restrict__ fits, int count) {
+    extern __shared__ double C[];
+    const Fit f = fits[blockIdx.x];
+    const int p = f.p, tid = threadIdx.x;
+    if (p > kBSmall || ((volatile Ctl*)f.ctl)->status != 0) return;
+    for (int idx = tid; idx < p * p; idx += kBThreads) {
+        const int a = idx / p, b = idx - a * p;
+        const int ia = f.order[a], ib = f.order[b];
+        C[idx] = f.sd[ia] * f.sd[ib] * f.sig0[size_t(ia) * p + ib];
+    }
+    __syncthreads();
+    for (int k = 0; k < p; ++k) {
+        const double ckk = C[k * p + k];
+        if (!(ckk > 0.0)) {   // every thread reads the same value: a uniform exit
+            if (tid == 0) set_status(f.ctl, LINGAM_EDEGENERATE);
+            return;
+        }
+        const double rk = sqrt(ckk);
+        __syncthreads();
+        for (int i = k + 1 + tid; i < p; i += kBThreads) C[i * p + k] /= rk;
+        if (tid == 0) C[k * p + k] = rk;
+        __syncthreads();
+        const int m = p - k - 1;
+        for (int idx = tid; idx < m * m; idx += kBThreads) {
+            const int i = k + 1 + idx / m, j = k + 1 + idx % m;
+            if (j <= i) C[i * p + j] -= C[i * p + k] * C[j * p + k];
+        }
+        __syncthreads();
+    }
+    double* y = f.rinv;   // column b of L^{-1} at y[b * p + a], a >= b
+    for (int b = tid; b < p; b += kBThreads) {
+        const int kb = f.order[b];
+        for (int a = 0; a < b; ++a) f.bout[size_t(f.order[a]) * p + kb] = 0.0;
+        for (int a = b; a < p; ++a) {
+            double acc = a == b ? 1.0 : 0.0;
+            for (int m2 = b; m2 < a; ++m2) acc = fma(-C[a * p + m2], y[size_t(b) * p + m2], acc);
+            const double ya = acc / C[a * p + a];
+            y[size_t(b) * p + a] = ya;
+            f.bout[size_t(f.order[a]) * p + kb] = a > b ? -C[a * p + a] * ya : 0.0;
+        }
+    }
+}
+
+cudaError_t launch_fit_B_batch(const Fit* fits_dev, const int* p_host, int count, const Fit* fits_host,
+                               cudaStream_t st) {
+    int pmax_small = 0;
+    for (int k = 0; k < count; ++k)
+        if (p_host[k] <= kBSmall && p_host[k] > pmax_small) pmax_small = p_host[k];
+    if (pmax_small > 0) {
+        const size_t smem = size_t(pmax_small) * pmax_small * sizeof(double);
+        cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(k_bfit_small), smem);
+        if (e != cudaSuccess) return e;
+        k_bfit_small<<<count, kBThreads, smem, st>>>(fits_dev, count);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    for (int k = 0; k < count; ++k)
+        if (p_host[k] > kBSmall) {
+            const cudaError_t e = launch_fit_B(fits_host[k], st);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
 cudaError_t launch_fit_B(const Fit& f, cudaStream_t st) {
     const int p = f.p;
     dim3 g2((p + 15) / 16, (p + 15) / 16);

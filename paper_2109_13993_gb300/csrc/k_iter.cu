@@ -574,6 +574,7 @@ __device__ __forceinline__ void acc2_add(Acc2& s, float2 u) {
 // Shared state of one CTA (besides the dynamic copy ring).
 struct IterShared {
     int red[32];
+    long long lred[33];
     int abort;
     int flag;
     double dred[32];
@@ -623,12 +624,25 @@ struct Wave {
     int ntiles, ncol, nrow;
 };
 
+// Where one problem's (tile, 32-sample group) units sit in the wave's stream-K
+// partition: the units of all problems of the wave are concatenated, this problem's
+// start at `off` of `utot`; G CTAs share them (unit_lo ranges); b_base is the first
+// CTA whose range reaches this problem.  A CTA's partial slot for tile t of the
+// problem is t + (b - b_base): unique within the problem, since the CTAs touching it
+// are contiguous and ordered like its units.  One problem alone: {0, U, G, 0}.
+struct Span {
+    long long off, utot, G;
+    int b_base;
+};
+__device__ __forceinline__ Span single_span(long long U, long long Gmax) {
+    return Span{0, U, working_ctas(U, Gmax), 0};
+}
+
 template <class Cfg>
-__device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, typename Cfg::T* ring, uint64_t* full, IterShared& sh,
-                              int& chunk_base) {
+__device__ __noinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wave& wv, const Span& sp,
+                                           typename Cfg::T* ring, uint64_t* full, IterShared& sh, int& chunk_base) {
     using T = typename Cfg::T;
     constexpr int CH = Cfg::CH, LDS = Cfg::LDS, TI = Cfg::TI, CONS = Cfg::CONS;
-    constexpr int NW = CONS / 32;
     constexpr bool kF32 = std::is_same<T, float>::value;
     Ctl* ctl = f.ctl;
     const int ntiles = wv.ntiles, ncol = wv.ncol, nrow = wv.nrow;
@@ -639,14 +653,17 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, typenam
     constexpr int GPC = CH / kSub;
     const int nch = f.ld / CH;
     const long long ng = (long long)nch * GPC;   // groups per tile
-    const long long U = (long long)ntiles * ng, G = working_ctas(U, gridDim.x);
+    const long long U = (long long)ntiles * ng;
     const int b = blockIdx.x;
-    if (b >= G) return true;   // no unit for this CTA in this wave
-    const long long g_lo = unit_lo(b, U, G), g_hi = unit_lo(b + 1, U, G);
+    if (b >= sp.G) return true;   // no unit for this CTA in this wave
+    const long long g_lo = max(0ll, unit_lo(b, sp.utot, sp.G) - sp.off);
+    const long long g_hi = min(U, unit_lo(b + 1, sp.utot, sp.G) - sp.off);
+    if (g_lo >= g_hi) return true;   // none of this problem's units
+    const int bs = b - sp.b_base;    // this CTA's partial slot offset within the problem
     const long long c_lo = g_lo / GPC;
     const int total = int((g_hi - 1) / GPC + 1 - c_lo);
-    const int tid = threadIdx.x, lane = tid & 31;
-    const unsigned long long tmo = ctl->timeout_ns;
+    const int tid = threadIdx.x;
+    const unsigned long long tmo = gctl->timeout_ns;
     const int base = chunk_base;   // ring position of this wave's first chunk
 
     int ctile = -1, cvar = -1;   // this thread's copy row (rows and columns changed with the wave)
@@ -704,7 +721,7 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, typenam
             g = min(seg_end, (cg + 1) * GPC);
             const int pos = base + k;
             const int s = pos % kStages;
-            const bool okw = mbar_wait_or_abort(&full[s], (pos / kStages) & 1, ctl, tmo, &sh.abort);
+            const bool okw = mbar_wait_or_abort(&full[s], (pos / kStages) & 1, gctl, tmo, &sh.abort);
             if (!okw) sh.abort = 1;
             const T* st = ring + size_t(s) * stage_elems<Cfg>();
             const T* R0 = st + rsl[0] * LDS;
@@ -821,8 +838,8 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, typenam
             __syncthreads();
             return false;
         }
-        // this CTA's partial moments of tile t: slot t + b
-        T* dst = parts + ((size_t(t) + b) * CONS + tid) * 16;
+        // this CTA's partial moments of tile t: slot t + bs
+        T* dst = parts + ((size_t(t) + bs) * CONS + tid) * 16;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             dst[4 * q + 0] = D[2 * q];
@@ -846,10 +863,10 @@ __device__ __noinline__ bool compute_phase(const Fit& f, const Wave& wv, typenam
 // (squared contributions summed in FP64), and the item that completes the wave's
 // last tile runs the wave finalisation.
 template <class Cfg>
-__device__ __noinline__ void merge_phase(const Fit& f, const Wave& wv, int it, IterShared& sh,
-                                         typename Cfg::T* scratch) {
+__device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span& sp, int it, IterShared& sh,
+                                        typename Cfg::T* scratch, int item) {
     using T = typename Cfg::T;
-    constexpr int CH = Cfg::CH, TI = Cfg::TI, CONS = Cfg::CONS;
+    constexpr int TI = Cfg::TI, CONS = Cfg::CONS;
     constexpr int NW = CONS / 32;
     constexpr int PARTS = CONS / 64;            // items per tile
     constexpr bool kF32 = std::is_same<T, float>::value;
@@ -857,17 +874,16 @@ __device__ __noinline__ void merge_phase(const Fit& f, const Wave& wv, int it, I
     const int ntiles = wv.ntiles, ncol = wv.ncol, nrow = wv.nrow;
     const int ld = f.ld;
     const long long ng = ld / kSub;   // 32-sample groups per tile: the stream-K unit
-    const long long U = (long long)ntiles * ng, G = working_ctas(U, gridDim.x);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const T* parts = static_cast<const T*>(f.partials);
     T* ibuf = static_cast<T*>(f.ibuf);
     const double n = double(f.n);
     const double pad_fix = double(ld - f.n) * kBeta;   // each zero padding sample added -beta
-    const int nitems = ntiles * PARTS;
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    {
         const int t = item / PARTS, part = item % PARTS;
-        const int b_first = cta_of_unit((long long)t * ng, U, G);
-        const int b_last = cta_of_unit((long long)(t + 1) * ng - 1, U, G);
+        // slot offsets of the CTAs that hold partial moments of tile t
+        const int b_first = cta_of_unit(sp.off + (long long)t * ng, sp.utot, sp.G) - sp.b_base;
+        const int b_last = cta_of_unit(sp.off + (long long)(t + 1) * ng - 1, sp.utot, sp.G) - sp.b_base;
         // 1. per warp: slots b_first + wid, + NW, ...; each lane 32 of the item's 1024 values
         T acc[32];
 #pragma unroll
@@ -975,17 +991,25 @@ __device__ __noinline__ void merge_phase(const Fit& f, const Wave& wv, int it, I
     }
 }
 
+// The merge of one problem's wave: its items spread over the CTAs.
+template <class Cfg>
+__device__ __forceinline__ void merge_phase(const Fit& f, const Wave& wv, const Span& sp, int it, IterShared& sh,
+                                            typename Cfg::T* scratch) {
+    const int nitems = wv.ntiles * (Cfg::CONS / 64);
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) merge_item<Cfg>(f, wv, sp, it, sh, scratch, item);
+}
+
 // ------------------------------------------------------------------ removal phases
 // UpdateData (Algorithm 7) with the new H(x_w) terms; rows of U spread over the CTAs.
 template <class Cfg>
-__device__ __noinline__ void remove_data_phase(const Fit& f, IterShared& sh) {
+__device__ __noinline__ void remove_data_phase(const Fit& f, IterShared& sh, int vb, int vG) {
     using T = typename Cfg::T;
     constexpr int NTH = Cfg::CONS;
     Ctl* ctl = f.ctl;
     volatile Ctl* vc = ctl;
     const int r = vc->r, root = vc->root, p = f.p, ld = f.ld, tid = threadIdx.x;
     const int lane = tid & 31, wid = tid >> 5;
-    for (int k = blockIdx.x; k < r; k += gridDim.x) {
+    for (int k = vb; k < r; k += vG) {
         const int w = ld2(f.sigma + k);
         if (tid == 0) f.prev[w] = ld2(f.part + w);
         if (w == root) {
@@ -1069,17 +1093,17 @@ __device__ __noinline__ void remove_data_phase(const Fit& f, IterShared& sh) {
 // Sigma is symmetric, so Sigma[j,root] is read from the root's row (contiguous).
 // The root's row and column are only read, so the update is done in place.
 template <class Cfg>
-__device__ __noinline__ void remove_cov_phase(const Fit& f) {
+__device__ __noinline__ void remove_cov_phase(const Fit& f, int vb, int vG) {
     constexpr int NTH = Cfg::CONS;
     volatile Ctl* vc = f.ctl;
     const int r = vc->r, root = vc->root, p = f.p, tid = threadIdx.x;
     const double* rootrow = f.sig + size_t(root) * p;
-    const int nmine = r > int(blockIdx.x) ? (r - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+    const int nmine = r > vb ? (r - 1 - vb) / vG + 1 : 0;
     const long long total = (long long)nmine * p;
 #pragma unroll 2
     for (long long idx = tid; idx < total; idx += NTH) {
         const int m = int(idx / p), j = int(idx - (long long)m * p);
-        const int w = ld2(f.sigma + blockIdx.x + m * gridDim.x);
+        const int w = ld2(f.sigma + vb + m * vG);
         if (w == root || j == root || !(ld2(f.flags + j) & kAlive)) continue;
         double* row = f.sig + size_t(w) * p;
         if (j == w) row[j] = 1.0;
@@ -1114,19 +1138,202 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
     int chunk_base = 0;
     while (!vc->done) {
         const Wave wv = {vc->ntiles, vc->ncol, vc->nrow};
-        if (!compute_phase<Cfg>(f, wv, ring, full, sh, chunk_base)) {
+        const Span sp = single_span((long long)wv.ntiles * (f.ld / kSub), gridDim.x);
+        if (!compute_phase<Cfg>(f, ctl, wv, sp, ring, full, sh, chunk_base)) {
             ctl->abort = 1;
             return;
         }
         if (!grid_sync(ctl, tmo)) return;
-        merge_phase<Cfg>(f, wv, it, sh, ring);
+        merge_phase<Cfg>(f, wv, sp, it, sh, ring);
         fence_proxy_async();   // the merge used the copy ring as scratch
         if (!grid_sync(ctl, tmo)) return;
     }
     if (it < f.p - 1 && vc->root >= 0) {
-        remove_data_phase<Cfg>(f, sh);
+        remove_data_phase<Cfg>(f, sh, blockIdx.x, gridDim.x);
         if (!grid_sync(ctl, tmo)) return;
-        remove_cov_phase<Cfg>(f);
+        remove_cov_phase<Cfg>(f, blockIdx.x, gridDim.x);
+    }
+}
+
+// ------------------------------------------------------------------ the batch kernel
+// Many independent problems (datasets of uneven p and n, or bootstrap resamples) in one
+// persistent cooperative launch: all iterations of all problems, in lockstep.  At
+// iteration it every problem with p > it is planned by one CTA; each wave then
+// concatenates the (tile, group) units of every problem whose iteration is not done
+// and partitions them over the grid (stream-K across problems, so a wave of many
+// small problems fills the GPU), merges each problem's tiles and runs its wave
+// finalisation; the removals of all problems share the grid.  A problem whose status
+// turns bad is not planned again (its outputs are not reported); a timeout or an
+// abort ends the whole launch.
+constexpr int kBatchMax = kBatchLaunchMax;   // problems per launch
+
+struct BatchShared {
+    long long uoff[kBatchMax + 1];   // first unit of each problem in this wave (prefix)
+    int ioff[kBatchMax + 1];         // first merge item of each problem in this wave
+    Wave wave[kBatchMax];            // each problem's wave, read at the wave's start
+    unsigned char act[kBatchMax];    // per problem: take part in this phase (one read per CTA)
+};
+
+// Which problems a CTA-wide phase of iteration it covers, read once per CTA into shared
+// memory so that every thread of the CTA takes the same branches (a problem's status can
+// change while other CTAs work on it).  removal = 0: planned (p > it, status good);
+// removal = 1: took a root this iteration and has rows left (it < p - 1).
+__device__ void batch_active(const Fit* fits, int count, int it, int removal, BatchShared& bs) {
+    for (int d = threadIdx.x; d < count; d += blockDim.x) {
+        const Fit& f = fits[d];
+        volatile Ctl* c = f.ctl;
+        bool a = it < f.p && c->status == 0;
+        if (removal) a = a && it < f.p - 1 && c->root >= 0;
+        bs.act[d] = a ? 1 : 0;
+    }
+    __syncthreads();
+}
+
+// Block-wide exclusive prefix sum of one value per thread; the total to every thread.
+template <int NTH>
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* lred, long long* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) lred[wid] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long run = 0;
+        for (int w = 0; w < NTH / 32; ++w) {
+            const long long t = lred[w];
+            lred[w] = run;
+            run += t;
+        }
+        lred[32] = run;
+    }
+    __syncthreads();
+    const long long ex = lred[wid] + x - v;
+    *total = lred[32];
+    __syncthreads();
+    return ex;
+}
+
+// The wave layout of all problems (every CTA computes the same one from the problems'
+// control blocks, which change only in the merge phase, between two grid barriers).
+template <int NTH, int TI>
+__device__ void batch_layout(const Fit* fits, int count, int it, BatchShared& bs, IterShared& sh, long long& utot,
+                             int& itot) {
+    long long ubase = 0, ibase = 0;
+    for (int base = 0; base < count; base += NTH) {
+        const int d = base + int(threadIdx.x);
+        long long u = 0, items = 0;
+        if (d < count) {
+            const Fit& f = fits[d];
+            volatile Ctl* c = f.ctl;
+            Wave w = {0, 0, 0};
+            if (it < f.p && !c->done) {
+                w = {c->ntiles, c->ncol, c->nrow};
+                u = (long long)w.ntiles * (f.ld / kSub);
+                items = (long long)w.ntiles * (NTH / 64);
+            }
+            bs.wave[d] = w;
+        }
+        long long tu, ti;
+        const long long eu = block_excl_scan<NTH>(u, sh.lred, &tu);
+        const long long ei = block_excl_scan<NTH>(items, sh.lred, &ti);
+        if (d < count) {
+            bs.uoff[d] = ubase + eu;
+            bs.ioff[d] = int(ibase + ei);
+        }
+        ubase += tu;
+        ibase += ti;
+    }
+    if (threadIdx.x == 0) {
+        bs.uoff[count] = ubase;
+        bs.ioff[count] = int(ibase);
+    }
+    __syncthreads();
+    utot = ubase;
+    itot = int(ibase);
+}
+
+// The last index d in [0, count) with off[d] <= v (off nondecreasing, off[0] = 0 <= v).
+template <class I>
+__device__ __forceinline__ int last_le(const I* off, int count, long long v) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((long long)off[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class Cfg>
+__global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __restrict__ fits, int count, int maxp,
+                                                               Ctl* bctl) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ IterShared sh;
+    __shared__ BatchShared bs;
+    using T = typename Cfg::T;
+    constexpr int CONS = Cfg::CONS, TI = Cfg::TI;
+    T* ring = reinterpret_cast<T*>(smem_raw);
+    const size_t ring_or_sort = ring_bytes<Cfg>() > size_t(kSortMax) * 8 ? ring_bytes<Cfg>() : size_t(kSortMax) * 8;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + ring_or_sort);
+    volatile Ctl* vb = bctl;
+    if (vb->status != 0) return;
+    const unsigned long long tmo = vb->timeout_ns;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+        sh.abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    int chunk_base = 0;   // ring position, continued over all waves of the launch
+    for (int it = 0; it < maxp; ++it) {
+        // plan (a problem whose status turned bad stays done: it is not planned again)
+        batch_active(fits, count, it, 0, bs);
+        for (int d = blockIdx.x; d < count; d += gridDim.x)
+            if (bs.act[d]) plan_phase<CONS, TI>(fits[d], it, smem_raw, sh.red);
+        if (!grid_sync(bctl, tmo)) return;
+        for (;;) {
+            long long utot;
+            int itot;
+            batch_layout<CONS, TI>(fits, count, it, bs, sh, utot, itot);
+            if (utot == 0) break;
+            const long long G = working_ctas(utot, gridDim.x);
+            const int b = blockIdx.x;
+            if (b < G) {
+                const long long lo = unit_lo(b, utot, G), hi = unit_lo(b + 1, utot, G);
+                for (int d = last_le(bs.uoff, count, lo); d < count && bs.uoff[d] < hi; ++d) {
+                    if (bs.uoff[d + 1] == bs.uoff[d]) continue;   // no units this wave
+                    const Span sp{bs.uoff[d], utot, G, cta_of_unit(bs.uoff[d], utot, G)};
+                    if (!compute_phase<Cfg>(fits[d], bctl, bs.wave[d], sp, ring, full, sh, chunk_base)) {
+                        bctl->abort = 1;
+                        return;
+                    }
+                }
+            }
+            if (!grid_sync(bctl, tmo)) return;
+            for (int gi = blockIdx.x; gi < itot; gi += gridDim.x) {
+                const int d = last_le(bs.ioff, count, gi);
+                const Span sp{bs.uoff[d], utot, G, cta_of_unit(bs.uoff[d], utot, G)};
+                merge_item<Cfg>(fits[d], bs.wave[d], sp, it, sh, ring, gi - bs.ioff[d]);
+            }
+            fence_proxy_async();   // the merge used the copy ring as scratch
+            if (!grid_sync(bctl, tmo)) return;
+        }
+        // UpdateData and UpdateCovMat of every problem that took a root.  Problem d's rows
+        // start at CTA (97 d) mod grid, a rotation fixed by d alone, so that every CTA
+        // agrees on the partition and the rows of many problems spread over the grid.
+        batch_active(fits, count, it, 1, bs);
+        for (int d = 0; d < count; ++d)
+            if (bs.act[d])
+                remove_data_phase<Cfg>(fits[d], sh, int((blockIdx.x + 97ull * d) % gridDim.x), gridDim.x);
+        if (!grid_sync(bctl, tmo)) return;
+        batch_active(fits, count, it, 1, bs);
+        for (int d = 0; d < count; ++d)
+            if (bs.act[d]) remove_cov_phase<Cfg>(fits[d], int((blockIdx.x + 97ull * d) % gridDim.x), gridDim.x);
+        if (!grid_sync(bctl, tmo)) return;
     }
 }
 
@@ -1161,6 +1368,35 @@ static cudaError_t launch_iter(const Fit& f, int it, int grid, cudaStream_t st) 
 cudaError_t launch_iteration(const Fit& f, int it, int grid, cudaStream_t st) {
     if (f.precision != LINGAM_MIXED) return launch_iter<CfgD>(f, it, grid, st);
     return f.tile_rows == 32 ? launch_iter<CfgF32>(f, it, grid, st) : launch_iter<CfgF64>(f, it, grid, st);
+}
+
+template <class Cfg>
+static cudaError_t launch_batch_cfg(const Fit* fits_dev, int count, int maxp, Ctl* bctl, int nsm, cudaStream_t st) {
+    const size_t smem = iter_smem_bytes<Cfg>();
+    cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(k_batch<Cfg>), smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<Cfg>, Cfg::CONS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nsm * (per_sm < Cfg::MINB ? per_sm : Cfg::MINB));
+    cfg.blockDim = dim3(Cfg::CONS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch<Cfg>, fits_dev, count, maxp, bctl);
+}
+
+cudaError_t launch_batch(const Fit* fits_dev, int count, int maxp, int precision, Ctl* bctl, int nsm,
+                         cudaStream_t st) {
+    if (count < 1 || count > kBatchMax) return cudaErrorInvalidValue;
+    return precision == LINGAM_MIXED ? launch_batch_cfg<CfgF64>(fits_dev, count, maxp, bctl, nsm, st)
+                                     : launch_batch_cfg<CfgD>(fits_dev, count, maxp, bctl, nsm, st);
 }
 
 }  // namespace lingam

@@ -14,6 +14,10 @@ cudaError_t ensure_smem_attr(const void* func, size_t bytes);
 // Normalise the rows of the input (NormalizeData, Algorithm 3), write the padded working copy,
 // the row moments and H(x) - H(nu).
 cudaError_t launch_standardize(const Fit& f, const void* x, int input_dtype, cudaStream_t st);
+// Batch start: per-problem init (orders unset, counters zero) and NormalizeData of all
+// rows of `count` problems (rowoff[d] = first global row of problem d, `rows` in all).
+cudaError_t launch_standardize_batch(const Fit* fits, const SrcDesc* src, const int* rowoff, int count, int rows,
+                                     int precision, int input_dtype, cudaStream_t st);
 // Sigma = Xn Xn^T / (n-1) of the normalised rows (CalculateCovMat, Algorithm 3); sig0 = sig.
 cudaError_t launch_gram(const Fit& f, cudaStream_t st);
 // The same product on the tensor cores (mixed path): the rows are split into exact
@@ -29,8 +33,18 @@ size_t gram_tc_partial_bytes(long long p, int ld);
 cudaError_t launch_iteration(const Fit& f, int it, int grid, cudaStream_t st);
 // Largest co-resident grid of the iteration kernel (one CTA per SM).
 int iteration_grid(const Fit& f, int nsm);
+// The ordering of up to 512 problems (a Fit table in device memory, each with its own
+// control block) in one persistent cooperative launch, all iterations, in lockstep;
+// bctl carries the launch's barrier, abort flag and timeout.
+cudaError_t launch_batch(const Fit* fits_dev, int count, int maxp, int precision, Ctl* bctl, int nsm,
+                         cudaStream_t st);
+constexpr int kBatchLaunchMax = 512;   // problems per launch_batch
 // B from the order: Cholesky of the covariance in causal order, B = I - diag(R) R^{-1}.
 cudaError_t launch_fit_B(const Fit& f, cudaStream_t st);
+// B of many problems: one CTA per problem of p <= 128 (shared-memory Cholesky), the
+// multi-launch fit for larger ones.  p_host and fits_host mirror the device table.
+cudaError_t launch_fit_B_batch(const Fit* fits_dev, const int* p_host, int count, const Fit* fits_host,
+                               cudaStream_t st);
 
 // Pair-tile autotuner (autotune.cu): the tile rows of the mixed path for a problem size,
 // recording a measured choice, and forgetting all of them.

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -129,29 +130,8 @@ static bool is_device_ptr(const void* ptr) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// cov_out != nullptr: stop after CalculateCovMat and copy Sigma (p x p) there.
-static int fit_one(const void* X, long long p_, long long n_, int* order, double* B, void* workspace,
-                   const lingam_opts& o, lingam_report* rep, double* cov_out = nullptr) {
-    if (!X || !(order || cov_out) || !workspace || p_ < 1 || n_ < 3 || p_ > kMaxP || n_ > (1ll << 30) || !valid_opts(o))
-        return LINGAM_EINVAL;
-    if (!is_device_ptr(workspace) || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return LINGAM_EINVAL;
-    const int p = int(p_), n = int(n_);
-    cudaStream_t st = static_cast<cudaStream_t>(o.stream);
-    const Layout L = make_layout(p_, n_, o.precision, o.input_dtype);
-    char* base = static_cast<char*>(workspace);
-
-    if (o.forced_order) {   // must be a permutation of 0..p-1
-        std::vector<char> seen(size_t(p), 0);
-        for (int k = 0; k < p; ++k) {
-            const int v = o.forced_order[k];
-            if (v < 0 || v >= p || seen[size_t(v)]) return LINGAM_EINVAL;
-            seen[size_t(v)] = 1;
-        }
-    }
-    int nsm = 0, dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return LINGAM_ECUDA;
-
+// The device view of one problem laid out in `base` (a workspace region of layout L).
+static Fit make_fit(char* base, const Layout& L, int p, int n, const lingam_opts& o, bool want_scores) {
     Fit f;
     std::memset(&f, 0, sizeof(f));
     f.p = p;
@@ -160,8 +140,7 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
     f.precision = o.precision;
     f.prune = o.prune;
     f.reuse = o.reuse;
-    f.has_forced = o.forced_order != nullptr;
-    f.want_scores = rep && rep->scores ? 1 : 0;
+    f.want_scores = want_scores ? 1 : 0;
     f.xt = base + L.off_xt;
     f.mu = reinterpret_cast<double*>(base + L.off_mu);
     f.sd = reinterpret_cast<double*>(base + L.off_sd);
@@ -175,7 +154,6 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
     f.rows = reinterpret_cast<int*>(base + L.off_rows);
     f.cols = reinterpret_cast<int*>(base + L.off_cols);
     f.order = reinterpret_cast<int*>(base + L.off_order);
-    f.forced = o.forced_order ? reinterpret_cast<const int*>(base + L.off_forced) : nullptr;
     f.scratch = reinterpret_cast<int*>(base + L.off_scratch);
     f.rowsum = reinterpret_cast<double*>(base + L.off_rowsum);
     f.colsum = reinterpret_cast<double*>(base + L.off_colsum);
@@ -195,6 +173,35 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
     f.maxtiles = L.maxtiles;
     f.maxsplit = L.maxsplit;
     f.tile_rows = o.precision == LINGAM_MIXED ? choose_tile_rows(p, n, o.tile_i) : 32;
+    return f;
+}
+
+// cov_out != nullptr: stop after CalculateCovMat and copy Sigma (p x p) there.
+static int fit_one(const void* X, long long p_, long long n_, int* order, double* B, void* workspace,
+                   const lingam_opts& o, lingam_report* rep, double* cov_out = nullptr) {
+    if (!X || !(order || cov_out) || !workspace || p_ < 1 || n_ < 3 || p_ > kMaxP || n_ > (1ll << 30) || !valid_opts(o))
+        return LINGAM_EINVAL;
+    if (!is_device_ptr(workspace) || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return LINGAM_EINVAL;
+    const int p = int(p_), n = int(n_);
+    cudaStream_t st = static_cast<cudaStream_t>(o.stream);
+    const Layout L = make_layout(p_, n_, o.precision, o.input_dtype);
+    char* base = static_cast<char*>(workspace);
+
+    if (o.forced_order) {   // must be a permutation of 0..p-1
+        std::vector<char> seen(static_cast<size_t>(p), 0);
+        for (int k = 0; k < p; ++k) {
+            const int v = o.forced_order[k];
+            if (v < 0 || v >= p || seen[size_t(v)]) return LINGAM_EINVAL;
+            seen[size_t(v)] = 1;
+        }
+    }
+    int nsm = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return LINGAM_ECUDA;
+
+    Fit f = make_fit(base, L, p, n, o, rep && rep->scores);
+    f.has_forced = o.forced_order != nullptr;
+    f.forced = o.forced_order ? reinterpret_cast<const int*>(base + L.off_forced) : nullptr;
 
 #define CK(call)                                  \
     do {                                          \
@@ -339,6 +346,324 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
 #undef CK
 }
 
+// ------------------------------------------------------------------ batches
+// Many independent problems (uneven datasets, or bootstrap resamples of one) share
+// one workspace: a header (the device Fit table, the problems' control blocks, the
+// batch control block, source descriptors, row offsets, output staging, and for
+// bootstraps the shared source and column indices), then one region per problem laid
+// out as for a single fit.  The device work (normalisation, covariance, one
+// persistent launch for all iterations of all problems, B) is captured once per
+// workspace and problem shape into a CUDA graph and replayed.
+struct BatchItem {
+    const void* X;        // source rows (host or device)
+    const int* idx;       // bootstrap: n column indices into the source row (device), else NULL
+    long long ld_src;     // row stride of the source, in elements
+    long long p, n;
+    int* order;
+    double* B;
+    lingam_report* rep;
+};
+
+struct BatchLayout {
+    size_t off_fits, off_ctls, off_bctl, off_src, off_rowoff, off_stage_order, off_stage_B, off_idx, off_xsrc;
+    size_t header, total;
+    std::vector<size_t> region;
+};
+
+static BatchLayout make_batch_layout(int count, const long long* p, const long long* n, const lingam_opts& o,
+                                     size_t idx_bytes, size_t xsrc_bytes) {
+    BatchLayout B;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    size_t sum_p = 0, sum_pp = 0;
+    for (int k = 0; k < count; ++k) {
+        sum_p += size_t(p[k]);
+        sum_pp += size_t(p[k]) * size_t(p[k]);
+    }
+    B.off_fits = take(size_t(count) * sizeof(Fit));
+    B.off_ctls = take(size_t(count) * sizeof(Ctl));
+    B.off_bctl = take(sizeof(Ctl));
+    B.off_src = take(size_t(count) * sizeof(SrcDesc));
+    B.off_rowoff = take(size_t(count + 1) * sizeof(int));
+    B.off_stage_order = take(sum_p * sizeof(int));
+    B.off_stage_B = take(sum_pp * sizeof(double));
+    B.off_idx = take(idx_bytes);
+    B.off_xsrc = take(xsrc_bytes);
+    B.header = off;
+    B.region.resize(size_t(count));
+    for (int k = 0; k < count; ++k) B.region[size_t(k)] = take(make_layout(p[k], n[k], o.precision, o.input_dtype).total);
+    B.total = off;
+    return B;
+}
+
+// Copies every problem's order (and B) into the staging area, back to back.
+__global__ void k_gather_outputs(const Fit* __restrict__ fits, int count, int* __restrict__ sorder,
+                                 double* __restrict__ sB, int with_B) {
+    const int d = blockIdx.x;
+    long long po = 0, pb = 0;
+    for (int e = 0; e < d; ++e) {
+        po += fits[e].p;
+        pb += (long long)fits[e].p * fits[e].p;
+    }
+    const Fit f = fits[d];
+    for (int k = threadIdx.x; k < f.p; k += blockDim.x) sorder[po + k] = f.order[k];
+    if (with_B)
+        for (long long k = threadIdx.x; k < (long long)f.p * f.p; k += blockDim.x) sB[pb + k] = f.bout[k];
+}
+
+struct GraphKey {
+    void* ws;
+    int count, precision, input_dtype, prune, reuse, with_B;
+    unsigned long long shape;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(ws, count, precision, input_dtype, prune, reuse, with_B, shape) <
+               std::tie(o.ws, o.count, o.precision, o.input_dtype, o.prune, o.reuse, o.with_B, o.shape);
+    }
+};
+static std::mutex g_graph_mu;
+static std::map<GraphKey, cudaGraphExec_t> g_graphs;
+
+static std::map<GraphKey, int> g_graph_seen;   // keys run once eagerly, captured on the next call
+
+// The device work of a batch, enqueued on st.
+static cudaError_t enqueue_batch(char* ws, const BatchLayout& BL, const std::vector<Fit>& fits,
+                                 const std::vector<Layout>& Ls, const lingam_opts& o, int rows, bool with_B,
+                                 bool gather, int nsm, cudaStream_t st) {
+    const int count = int(fits.size());
+    const Fit* fits_dev = reinterpret_cast<const Fit*>(ws + BL.off_fits);
+    cudaError_t e = launch_standardize_batch(fits_dev, reinterpret_cast<const SrcDesc*>(ws + BL.off_src),
+                                             reinterpret_cast<const int*>(ws + BL.off_rowoff), count, rows,
+                                             o.precision, o.input_dtype, st);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < count; ++k) {
+        e = o.precision == LINGAM_MIXED
+                ? launch_gram_tc(fits[size_t(k)], ws + BL.region[size_t(k)] + Ls[size_t(k)].off_xin, fits[size_t(k)].partials, st)
+                : launch_gram(fits[size_t(k)], st);
+        if (e != cudaSuccess) return e;
+    }
+    Ctl* bctl = reinterpret_cast<Ctl*>(ws + BL.off_bctl);
+    for (int c0 = 0; c0 < count; c0 += kBatchLaunchMax) {
+        const int cnt = std::min(kBatchLaunchMax, count - c0);
+        int maxp = 0;
+        for (int k = c0; k < c0 + cnt; ++k) maxp = std::max(maxp, fits[size_t(k)].p);
+        e = launch_batch(fits_dev + c0, cnt, maxp, o.precision, bctl, nsm, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (with_B) {
+        std::vector<int> ph(static_cast<size_t>(count));
+        for (int k = 0; k < count; ++k) ph[size_t(k)] = fits[size_t(k)].p;
+        e = launch_fit_B_batch(fits_dev, ph.data(), count, fits.data(), st);
+        if (e != cudaSuccess) return e;
+    }
+    if (gather) {
+        k_gather_outputs<<<count, 256, 0, st>>>(fits_dev, count, reinterpret_cast<int*>(ws + BL.off_stage_order),
+                                                reinterpret_cast<double*>(ws + BL.off_stage_B), with_B ? 1 : 0);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+// Bootstrap source shared by all problems of a batch (NULL X for plain batches).
+struct BootSrc {
+    const void* X;       // p x n_src rows, host or device
+    const int* idx;      // nboot x n column indices, host or device
+    long long p, n_src, n;
+    int nboot;
+};
+
+static int fit_many(std::vector<BatchItem>& items, void* workspace, const lingam_opts& o, int* status_out,
+                    const BootSrc* boot) {
+    const int count = int(items.size());
+    if (count == 0) return LINGAM_OK;
+    if (!valid_opts(o) || o.forced_order || o.max_iters != 0 || !workspace) return LINGAM_EINVAL;
+    if (!is_device_ptr(workspace) || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return LINGAM_EINVAL;
+    std::vector<long long> P(static_cast<size_t>(count)), N(static_cast<size_t>(count));
+    bool with_B = true, gather = true;
+    for (int k = 0; k < count; ++k) {
+        const BatchItem& it = items[size_t(k)];
+        if (!it.X || !it.order || it.p < 1 || it.n < 3 || it.p > kMaxP || it.n > (1ll << 30)) return LINGAM_EINVAL;
+        P[size_t(k)] = it.p;
+        N[size_t(k)] = it.n;
+        if (!it.B) with_B = false;
+        if (is_device_ptr(it.order) || (it.B && is_device_ptr(it.B))) gather = false;
+    }
+    const size_t esz = o.input_dtype == LINGAM_F32 ? 4 : 8;
+    const size_t idx_bytes = boot ? size_t(boot->nboot) * size_t(boot->n) * sizeof(int) : 0;
+    const size_t xsrc_bytes = boot ? size_t(boot->p) * size_t(boot->n_src) * esz : 0;
+    const BatchLayout BL = make_batch_layout(count, P.data(), N.data(), o, idx_bytes, xsrc_bytes);
+    char* ws = static_cast<char*>(workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(o.stream);
+    int nsm = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return LINGAM_ECUDA;
+#define CKB(call)                     \
+    do {                              \
+        if ((call) != cudaSuccess) {  \
+            cudaGetLastError();       \
+            return LINGAM_ECUDA;      \
+        }                             \
+    } while (0)
+
+    // bootstrap source rows and column indices (copied once into the header when on the host)
+    const void* boot_x = nullptr;
+    const int* boot_idx = nullptr;
+    if (boot) {
+        boot_x = boot->X;
+        if (!is_device_ptr(boot->X)) {
+            CKB(cudaMemcpyAsync(ws + BL.off_xsrc, boot->X, xsrc_bytes, cudaMemcpyHostToDevice, st));
+            boot_x = ws + BL.off_xsrc;
+        }
+        boot_idx = boot->idx;
+        if (!is_device_ptr(boot->idx)) {
+            CKB(cudaMemcpyAsync(ws + BL.off_idx, boot->idx, idx_bytes, cudaMemcpyHostToDevice, st));
+            boot_idx = reinterpret_cast<const int*>(ws + BL.off_idx);
+        }
+    }
+    std::vector<char> H(BL.off_stage_order, 0);
+    std::vector<Fit> fits(static_cast<size_t>(count));
+    std::vector<Layout> Ls(static_cast<size_t>(count));
+    Ctl c0;
+    std::memset(&c0, 0, sizeof(c0));
+    const double tmo = o.timeout_s > 0 ? o.timeout_s : 10.0;
+    c0.timeout_ns = (unsigned long long)(tmo * 1e9);
+    c0.root = -1;
+    int rows = 0;
+    unsigned long long shape = 1469598103934665603ull;   // FNV-1a over the problem shapes
+    auto mix = [&](long long v) {
+        shape ^= (unsigned long long)v;
+        shape *= 1099511628211ull;
+    };
+    for (int k = 0; k < count; ++k) {
+        BatchItem& it = items[size_t(k)];
+        char* base = ws + BL.region[size_t(k)];
+        Ls[size_t(k)] = make_layout(it.p, it.n, o.precision, o.input_dtype);
+        const Layout& L = Ls[size_t(k)];
+        Fit f = make_fit(base, L, int(it.p), int(it.n), o, it.rep && it.rep->scores);
+        f.ctl = reinterpret_cast<Ctl*>(ws + BL.off_ctls) + k;
+        f.tile_rows = o.precision == LINGAM_MIXED ? 64 : 32;   // the batch kernel's tile shape
+        fits[size_t(k)] = f;
+        SrcDesc sd;
+        if (boot) {
+            sd.x = boot_x;
+            sd.idx = boot_idx + size_t(k) * size_t(it.n);
+            sd.ld = it.ld_src;
+        } else {
+            sd.x = it.X;
+            if (!is_device_ptr(it.X)) {
+                CKB(cudaMemcpyAsync(base + L.off_xin, it.X, size_t(it.p) * size_t(it.n) * esz, cudaMemcpyHostToDevice, st));
+                sd.x = base + L.off_xin;
+            }
+            sd.idx = nullptr;
+            sd.ld = it.n;
+        }
+        std::memcpy(H.data() + BL.off_fits + size_t(k) * sizeof(Fit), &f, sizeof(Fit));
+        std::memcpy(H.data() + BL.off_ctls + size_t(k) * sizeof(Ctl), &c0, sizeof(Ctl));
+        std::memcpy(H.data() + BL.off_src + size_t(k) * sizeof(SrcDesc), &sd, sizeof(SrcDesc));
+        std::memcpy(H.data() + BL.off_rowoff + size_t(k) * sizeof(int), &rows, sizeof(int));
+        rows += int(it.p);
+        mix(it.p);
+        mix(it.n);
+        mix(it.ld_src);
+        mix(it.rep && it.rep->scores ? 1 : 0);
+    }
+    std::memcpy(H.data() + BL.off_rowoff + size_t(count) * sizeof(int), &rows, sizeof(int));
+    std::memcpy(H.data() + BL.off_bctl, &c0, sizeof(Ctl));
+    // the tables at the head of the header (the staging and bootstrap areas follow them)
+    CKB(cudaMemcpyAsync(ws, H.data(), BL.off_stage_order, cudaMemcpyHostToDevice, st));
+
+    // the device work: eagerly on a key's first call (and on the legacy stream), from a
+    // captured graph afterwards
+    const GraphKey key{workspace, count, o.precision, o.input_dtype, o.prune, o.reuse, (with_B ? 1 : 0) | (gather ? 2 : 0) | (boot ? 4 : 0), shape};
+    cudaGraphExec_t exec = nullptr;
+    bool capture = false;
+    if (st != nullptr) {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        auto itg = g_graphs.find(key);
+        if (itg != g_graphs.end()) exec = itg->second;
+        else if (g_graph_seen.count(key)) capture = true;
+        else g_graph_seen[key] = 1;
+    }
+    if (exec) {
+        CKB(cudaGraphLaunch(exec, st));
+    } else if (capture) {
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        const cudaError_t eq = ok ? enqueue_batch(ws, BL, fits, Ls, o, rows, with_B, gather, nsm, st) : cudaErrorUnknown;
+        if (ok) ok = cudaStreamEndCapture(st, &graph) == cudaSuccess && eq == cudaSuccess;
+        if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (ok) {
+            std::lock_guard<std::mutex> lk(g_graph_mu);
+            g_graphs[key] = exec;
+            CKB(cudaGraphLaunch(exec, st));
+        } else {
+            CKB(enqueue_batch(ws, BL, fits, Ls, o, rows, with_B, gather, nsm, st));
+        }
+    } else {
+        CKB(enqueue_batch(ws, BL, fits, Ls, o, rows, with_B, gather, nsm, st));
+    }
+    CKB(cudaStreamSynchronize(st));
+
+    // statuses and outputs
+    std::vector<Ctl> ctls(static_cast<size_t>(count));
+    Ctl bc;
+    CKB(cudaMemcpy(ctls.data(), ws + BL.off_ctls, size_t(count) * sizeof(Ctl), cudaMemcpyDeviceToHost));
+    CKB(cudaMemcpy(&bc, ws + BL.off_bctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    std::vector<int> sorder;
+    std::vector<double> sB;
+    if (gather) {
+        size_t sp = 0, spp = 0;
+        for (int k = 0; k < count; ++k) {
+            sp += size_t(P[size_t(k)]);
+            spp += size_t(P[size_t(k)]) * size_t(P[size_t(k)]);
+        }
+        sorder.resize(sp);
+        CKB(cudaMemcpy(sorder.data(), ws + BL.off_stage_order, sp * sizeof(int), cudaMemcpyDeviceToHost));
+        if (with_B) {
+            sB.resize(spp);
+            CKB(cudaMemcpy(sB.data(), ws + BL.off_stage_B, spp * sizeof(double), cudaMemcpyDeviceToHost));
+        }
+    }
+    int first = LINGAM_OK;
+    size_t po = 0, pb = 0;
+    for (int k = 0; k < count; ++k) {
+        const BatchItem& it = items[size_t(k)];
+        const Fit& f = fits[size_t(k)];
+        const size_t pk = size_t(it.p);
+        int stk = bc.status != 0 ? bc.status : ctls[size_t(k)].status;
+        if (stk == LINGAM_OK) {
+            if (gather) {
+                std::memcpy(it.order, sorder.data() + po, pk * sizeof(int));
+                if (with_B) std::memcpy(it.B, sB.data() + pb, pk * pk * sizeof(double));
+            } else {
+                if (cudaMemcpy(it.order, f.order, pk * sizeof(int), cudaMemcpyDefault) != cudaSuccess) stk = LINGAM_ECUDA;
+                if (with_B && cudaMemcpy(it.B, f.bout, pk * pk * sizeof(double), cudaMemcpyDefault) != cudaSuccess)
+                    stk = LINGAM_ECUDA;
+            }
+            if (it.rep) {
+                lingam_report* r = it.rep;
+                if (r->root_score) cudaMemcpy(r->root_score, f.rep_root_score, pk * 8, cudaMemcpyDefault);
+                if (r->margin_lb) cudaMemcpy(r->margin_lb, f.rep_margin, pk * 8, cudaMemcpyDefault);
+                if (r->pairs_evaluated) cudaMemcpy(r->pairs_evaluated, f.rep_pairs, pk * 8, cudaMemcpyDefault);
+                if (r->scores) cudaMemcpy(r->scores, f.rep_scores, pk * pk * 8, cudaMemcpyDefault);
+                r->t_standardize_ms = r->t_gram_ms = r->t_order_ms = r->t_B_ms = r->t_pair_ms = -1.0;
+            }
+        }
+        po += pk;
+        pb += pk * pk;
+        if (status_out) status_out[k] = stk;
+        if (stk != LINGAM_OK && first == LINGAM_OK) first = stk;
+    }
+    cudaGetLastError();
+    return first;
+#undef CKB
+}
+
 }  // namespace lingam
 
 using namespace lingam;
@@ -417,14 +742,13 @@ int lingam_autotune(const void* X, long long p, long long n, void* workspace, co
 void lingam_autotune_reset(void) { autotune_clear(); }
 
 size_t lingam_workspace_size_batch(int count, const long long* p, const long long* n, const lingam_opts* opts) {
-    if (count < 0 || (count > 0 && (!p || !n))) return 0;
-    size_t tot = 0;
-    for (int k = 0; k < count; ++k) {
-        const size_t s = lingam_workspace_size(p[k], n[k], opts);
-        if (s == 0) return 0;
-        tot += align_up(s);
-    }
-    return tot;
+    lingam_opts o;
+    lingam_default_opts(&o);
+    if (opts) o = *opts;
+    if (count < 0 || (count > 0 && (!p || !n)) || !valid_opts(o)) return 0;
+    for (int k = 0; k < count; ++k)
+        if (p[k] < 1 || n[k] < 3 || p[k] > kMaxP || n[k] > (1ll << 30)) return 0;
+    return make_batch_layout(count, p, n, o, 0, 0).total;
 }
 
 int lingam_fit_batch(int count, const void* const* X, const long long* p, const long long* n, int* const* order,
@@ -433,19 +757,43 @@ int lingam_fit_batch(int count, const void* const* X, const long long* p, const 
     lingam_opts o;
     lingam_default_opts(&o);
     if (opts) o = *opts;
-    if (o.forced_order) return LINGAM_EINVAL;
-    int first = LINGAM_OK;
-    size_t off = 0;
-    for (int k = 0; k < count; ++k) {
-        const size_t s = lingam_workspace_size(p[k], n[k], &o);
-        int st = s == 0 ? LINGAM_EINVAL
-                        : fit_one(X[k], p[k], n[k], order[k], B ? B[k] : nullptr, static_cast<char*>(workspace) + off, o,
-                                  report ? &report[k] : nullptr);
-        off += align_up(s);
-        if (status) status[k] = st;
-        if (st != LINGAM_OK && first == LINGAM_OK) first = st;
+    std::vector<BatchItem> items(static_cast<size_t>(count));
+    for (int k = 0; k < count; ++k)
+        items[size_t(k)] = BatchItem{X[k], nullptr, n[k], p[k], n[k], order[k], B ? B[k] : nullptr,
+                                     report ? &report[k] : nullptr};
+    return fit_many(items, workspace, o, status, nullptr);
+}
+
+size_t lingam_workspace_size_bootstrap(long long p, long long n, int nboot, const lingam_opts* opts) {
+    lingam_opts o;
+    lingam_default_opts(&o);
+    if (opts) o = *opts;
+    if (nboot < 1 || p < 1 || n < 3 || p > kMaxP || n > (1ll << 30) || !valid_opts(o)) return 0;
+    std::vector<long long> P(static_cast<size_t>(nboot), p), N(static_cast<size_t>(nboot), n);
+    const size_t esz = o.input_dtype == LINGAM_F32 ? 4 : 8;
+    return make_batch_layout(nboot, P.data(), N.data(), o, size_t(nboot) * size_t(n) * sizeof(int),
+                             size_t(p) * size_t(n) * esz)
+        .total;
+}
+
+int lingam_fit_bootstrap(const void* X, long long p, long long n, int nboot, const int* idx, int* order, double* B,
+                         void* workspace, const lingam_opts* opts, int* status, lingam_report* report) {
+    if (!X || !idx || !order || !workspace || nboot < 1 || p < 1 || n < 3 || p > kMaxP || n > (1ll << 30))
+        return LINGAM_EINVAL;
+    lingam_opts o;
+    lingam_default_opts(&o);
+    if (opts) o = *opts;
+    if (!is_device_ptr(idx)) {   // indices must lie in [0, n)
+        for (long long k = 0; k < (long long)nboot * n; ++k)
+            if (idx[k] < 0 || idx[k] >= n) return LINGAM_EINVAL;
     }
-    return first;
+    std::vector<BatchItem> items(static_cast<size_t>(nboot));
+    for (int k = 0; k < nboot; ++k)
+        items[size_t(k)] = BatchItem{X, nullptr, n, p, n, order + size_t(k) * size_t(p),
+                                     B ? B + size_t(k) * size_t(p) * size_t(p) : nullptr,
+                                     report ? &report[k] : nullptr};
+    const BootSrc boot{X, idx, p, n, n, nboot};
+    return fit_many(items, workspace, o, status, &boot);
 }
 
 const char* lingam_status_string(int s) {

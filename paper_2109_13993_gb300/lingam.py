@@ -76,6 +76,13 @@ def load():
                                    ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
                                    ctypes.POINTER(Opts), _c_int_p, ctypes.POINTER(Report)]
     L.lingam_fit_batch.restype = ctypes.c_int
+    L.lingam_workspace_size_bootstrap.argtypes = [ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int,
+                                                  ctypes.POINTER(Opts)]
+    L.lingam_workspace_size_bootstrap.restype = ctypes.c_size_t
+    L.lingam_fit_bootstrap.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.POINTER(Opts), _c_int_p, ctypes.POINTER(Report)]
+    L.lingam_fit_bootstrap.restype = ctypes.c_int
     L.lingam_fit_static.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.POINTER(Report)]
     L.lingam_fit_static.restype = ctypes.c_int
@@ -283,31 +290,115 @@ def autotune_reset():
     load().lingam_autotune_reset()
 
 
-def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = True, stream=None):
-    """lingam_fit_batch over a list of data sets (numpy or torch, each p_k x n_k)."""
+def _reports(count, ps, want_report):
+    """Report structs with host arrays for root scores, margins and pair counts."""
+    if not want_report:
+        return None, None
+    reps = (Report * count)()
+    keep = []
+    for k in range(count):
+        rs, mg, pe = np.zeros(ps[k]), np.zeros(ps[k]), np.zeros(ps[k], dtype=np.int64)
+        reps[k].root_score = rs.ctypes.data_as(_c_dbl_p)
+        reps[k].margin_lb = mg.ctypes.data_as(_c_dbl_p)
+        reps[k].pairs_evaluated = pe.ctypes.data_as(_c_ll_p)
+        keep.append((rs, mg, pe))
+    return reps, keep
+
+
+@dataclass
+class BatchResult:
+    status: int                    # first non-OK dataset status, else LINGAM_OK
+    statuses: np.ndarray           # per dataset
+    orders: list                   # per dataset, int32 [p]
+    Bs: list | None                # per dataset, float64 [p, p]
+    root_scores: list | None = None
+    margins: list | None = None
+    pairs: list | None = None
+
+
+def batch_workspace(ps, ns, precision: str = "mixed", input_dtype=np.float32):
+    """A device workspace for lingam_fit_batch over datasets of sizes ps[k] x ns[k];
+    pass it to every call on these shapes to let the library replay its CUDA graph."""
+    L = load()
+    o, _ = make_opts(precision, input_dtype)
+    count = len(ps)
+    pa = (ctypes.c_longlong * count)(*ps)
+    na = (ctypes.c_longlong * count)(*ns)
+    need = int(L.lingam_workspace_size_batch(count, pa, na, ctypes.byref(o)))
+    if need == 0:
+        raise LingamError(LINGAM_EINVAL, "invalid sizes or options")
+    return alloc_workspace(need)
+
+
+def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = True, stream=None, workspace=None,
+              want_report: bool = False) -> BatchResult:
+    """lingam_fit_batch over a list of datasets (numpy or torch, each p_k x n_k, one dtype)."""
     L = load()
     torch = _torch()
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     items = [_data_ptr(X) for X in Xs]
     count = len(items)
-    dts = {it[3] for it in items}
-    if len(dts) > 1:
-        raise TypeError("all data sets of a batch must share one dtype")
+    if len({it[3] for it in items}) > 1:
+        raise TypeError("all datasets of a batch must share one dtype")
     o, _ = make_opts(precision, items[0][3] if items else np.float32, prune, True, 0, 10.0, stream)
-    ps = (ctypes.c_longlong * count)(*[it[1] for it in items])
-    ns = (ctypes.c_longlong * count)(*[it[2] for it in items])
-    need = int(L.lingam_workspace_size_batch(count, ps, ns, ctypes.byref(o)))
-    ws = alloc_workspace(need)
-    orders = [np.zeros(it[1], dtype=np.int32) for it in items]
-    Bs = [np.zeros((it[1], it[1])) for it in items] if want_B else None
+    ps = [it[1] for it in items]
+    ns = [it[2] for it in items]
+    pa = (ctypes.c_longlong * count)(*ps)
+    na = (ctypes.c_longlong * count)(*ns)
+    need = int(L.lingam_workspace_size_batch(count, pa, na, ctypes.byref(o)))
+    if need == 0:
+        raise LingamError(LINGAM_EINVAL, "invalid sizes or options")
+    if workspace is None or workspace.numel() < need:
+        workspace = alloc_workspace(need)
+    orders = [np.zeros(p, dtype=np.int32) for p in ps]
+    Bs = [np.zeros((p, p)) for p in ps] if want_B else None
     xp = (ctypes.c_void_p * count)(*[it[0] for it in items])
     op = (ctypes.c_void_p * count)(*[o_.ctypes.data for o_ in orders])
     bp = (ctypes.c_void_p * count)(*[b.ctypes.data for b in Bs]) if Bs is not None else None
     status = np.zeros(count, dtype=np.int32)
-    st = L.lingam_fit_batch(count, xp, ps, ns, op, bp, ctypes.c_void_p(ws.data_ptr()), ctypes.byref(o),
-                            status.ctypes.data_as(_c_int_p), None)
-    return st, status, orders, Bs
+    reps, keep_rep = _reports(count, ps, want_report)
+    st = L.lingam_fit_batch(count, xp, pa, na, op, bp, ctypes.c_void_p(workspace.data_ptr()), ctypes.byref(o),
+                            status.ctypes.data_as(_c_int_p), reps)
+    del items
+    res = BatchResult(status=int(st), statuses=status, orders=orders, Bs=Bs)
+    if keep_rep:
+        res.root_scores = [k[0] for k in keep_rep]
+        res.margins = [k[1] for k in keep_rep]
+        res.pairs = [k[2] for k in keep_rep]
+    return res
+
+
+def fit_bootstrap(X, idx, precision: str = "mixed", prune: bool = True, want_B: bool = True, stream=None,
+                  workspace=None) -> BatchResult:
+    """lingam_fit_bootstrap: X (p x n), idx (nboot x n column indices, numpy or CUDA tensor)."""
+    L = load()
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    ptr, p, n, dt, keep = _data_ptr(X)
+    if isinstance(idx, np.ndarray):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        iptr, nboot = idx.ctypes.data, idx.shape[0]
+    else:
+        idx = idx.to(torch.int32).contiguous()
+        iptr, nboot = idx.data_ptr(), idx.shape[0]
+    if idx.shape[1] != n:
+        raise ValueError("idx must be nboot x n")
+    o, _ = make_opts(precision, dt, prune, True, 0, 10.0, stream)
+    need = int(L.lingam_workspace_size_bootstrap(p, n, nboot, ctypes.byref(o)))
+    if need == 0:
+        raise LingamError(LINGAM_EINVAL, "invalid sizes or options")
+    if workspace is None or workspace.numel() < need:
+        workspace = alloc_workspace(need)
+    order = np.zeros((nboot, p), dtype=np.int32)
+    B = np.zeros((nboot, p, p)) if want_B else None
+    status = np.zeros(nboot, dtype=np.int32)
+    st = L.lingam_fit_bootstrap(ctypes.c_void_p(ptr), p, n, nboot, ctypes.c_void_p(iptr), order.ctypes.data,
+                                B.ctypes.data if B is not None else None, ctypes.c_void_p(workspace.data_ptr()),
+                                ctypes.byref(o), status.ctypes.data_as(_c_int_p), None)
+    del keep
+    return BatchResult(status=int(st), statuses=status, orders=list(order), Bs=list(B) if B is not None else None)
 
 
 STATIC_SCRATCH_BYTES = 32 << 20   # LINGAM_STATIC_SCRATCH_BYTES in include/lingam.h

@@ -72,3 +72,38 @@ def test_tile_rows_default_rule(lib):
     for bad in (16, 48, 128):
         o.tile_i = bad
         assert lib.lingam_workspace_size(10, 100, ctypes.byref(o)) == 0
+
+
+def test_batch_and_bootstrap_workspace_sizes(lib):
+    ps = (ctypes.c_longlong * 3)(10, 20, 50)
+    ns = (ctypes.c_longlong * 3)(100, 200, 2000)
+    tot = lib.lingam_workspace_size_batch(3, ps, ns, None)
+    assert tot >= sum(lingam.workspace_size(p, n) for p, n in zip(ps, ns))
+    assert tot % 256 == 0
+    bad = (ctypes.c_longlong * 3)(10, 0, 50)
+    assert lib.lingam_workspace_size_batch(3, bad, ns, None) == 0
+    o, _ = lingam.make_opts()
+    b = lib.lingam_workspace_size_bootstrap(50, 2000, 256, ctypes.byref(o))
+    # the resample regions plus the shared source (p n floats) and the indices (nboot n ints)
+    assert b >= 256 * lingam.workspace_size(50, 2000) + 50 * 2000 * 4 + 256 * 2000 * 4
+    assert lib.lingam_workspace_size_bootstrap(50, 2000, 0, ctypes.byref(o)) == 0
+
+
+def test_batch_rejects_bad_arguments_without_gpu_work(lib):
+    x = np.zeros((3, 10), dtype=np.float32)
+    xp = (ctypes.c_void_p * 1)(x.ctypes.data)
+    ps = (ctypes.c_longlong * 1)(3)
+    ns = (ctypes.c_longlong * 1)(10)
+    order = np.zeros(3, dtype=np.int32)
+    op = (ctypes.c_void_p * 1)(order.ctypes.data)
+    # no workspace, then a host "workspace": both rejected before any device work
+    assert lib.lingam_fit_batch(1, xp, ps, ns, op, None, None, None, None, None) == lingam.LINGAM_EINVAL
+    ws = np.zeros(1 << 20, dtype=np.uint8)
+    st = np.zeros(1, dtype=np.int32)
+    assert lib.lingam_fit_batch(1, xp, ps, ns, op, None, ctypes.c_void_p(ws.ctypes.data), None,
+                                st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), None) == lingam.LINGAM_EINVAL
+    idx = np.full((2, 10), 11, dtype=np.int32)   # out of range
+    o2 = np.zeros((2, 3), dtype=np.int32)
+    assert lib.lingam_fit_bootstrap(ctypes.c_void_p(x.ctypes.data), 3, 10, 2, ctypes.c_void_p(idx.ctypes.data),
+                                    ctypes.c_void_p(o2.ctypes.data), None, ctypes.c_void_p(ws.ctypes.data), None,
+                                    None, None) == lingam.LINGAM_EINVAL

@@ -1,0 +1,195 @@
+"""Batches through lingam_fit_batch and lingam_fit_bootstrap: many independent
+problems in one persistent launch (and, from the second call on the same
+workspace and shapes, from a captured CUDA graph).
+
+A problem's result in a batch differs from its single fit only in how its
+pairs' samples are grouped into partial sums (the stream-K partition spans all
+problems), i.e. in FP32 rounding.  So orders must agree with the single fit (or
+the oracle) on every iteration the reference's margin resolves, and may differ
+after the first unresolved one.  The per-score bound of the mixed path is
+tau = kappa sqrt(m S) + m (2e-6)^2 with kappa = 1e-5 (the bound asserted by the
+single-fit parity tests, which measure about 2e-6).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_13993_gb300 import lingam, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+KAPPA = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2109_13993_gb300 import build
+    build.build()
+    lingam.load()
+    oracle.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _dev(X, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(X), dtype=dtype, device="cuda")
+
+
+def _tau(S, m):
+    return KAPPA * np.sqrt(max(m, 1) * max(S, 0.0)) + max(m, 1) * (2e-6) ** 2
+
+
+def _agree_until_unresolved(order, ref_order, ref_root, ref_margin):
+    """The orders agree up to their first difference, and that iteration's reference
+    margin is within the two scores' bounds (a resolved iteration never differs).
+    Returns the length of the common prefix."""
+    p = len(ref_order)
+    for it in range(p):
+        if order[it] != ref_order[it]:
+            m = p - it - 1
+            tau1 = _tau(ref_root[it], m)
+            tau2 = _tau(ref_root[it] + ref_margin[it], m)
+            assert not ref_margin[it] > tau1 + tau2, f"resolved iteration {it} differs"
+            return it
+    return p
+
+
+def _single(X):
+    """Reference single fit with complete scores (no pruning): exact roots and margins."""
+    r = lingam.fit(X, precision="mixed", prune=False, want_scores=True)
+    roots, margins = _oracle_margins(r.scores)
+    return r, roots, margins
+
+
+def _oracle_margins(S):
+    roots, margins = [], []
+    for row in S:
+        v = np.sort(row[~np.isnan(row)])
+        roots.append(v[0])
+        margins.append(v[1] - v[0] if len(v) > 1 else np.inf)
+    return np.array(roots), np.array(margins)
+
+
+def test_batch_matches_single_fits():
+    ds = synth.uneven_batch(6, seed=4)
+    Xs = [_dev(d.X[:, : min(d.X.shape[1], 3000)].astype(np.float32)) for d in ds]
+    res = lingam.fit_batch(Xs, precision="mixed")
+    assert res.status == 0 and np.all(res.statuses == 0)
+    for X, o, B in zip(Xs, res.orders, res.Bs):
+        single, roots, margins = _single(X)
+        k = _agree_until_unresolved(o, single.order, roots, margins)
+        print(f"p={X.shape[0]} n={X.shape[1]}: batch order equals the single fit on {k} of {len(o)} iterations")
+        if k == len(o):
+            assert np.abs(B - single.B).max() <= 1e-6 * max(1.0, np.abs(single.B).max())
+
+
+def test_batch_matches_oracle():
+    sizes = [(5, 4000), (12, 3000), (20, 2000), (33, 2500)]
+    Xs, ds = [], []
+    for k, (p, n) in enumerate(sizes):
+        d = synth.lingam_dataset(p, n, min(1.0, 4.0 / (p - 1)), seed=40 + k)
+        ds.append(d.X.astype(np.float32))
+        Xs.append(_dev(ds[-1]))
+    res = lingam.fit_batch(Xs, precision="mixed", want_report=True)
+    assert res.status == 0
+    for X32, o, B in zip(ds, res.orders, res.Bs):
+        o_order, o_B, o_S = oracle.fit(X32.astype(np.float64))
+        roots, margins = _oracle_margins(o_S)
+        k = _agree_until_unresolved(o, o_order, roots, margins)
+        print(f"p={X32.shape[0]}: batch order equals the oracle on {k} of {len(o)} iterations")
+        if k == len(o):
+            assert np.abs(B - o_B).max() <= 1e-4 * max(1.0, np.abs(o_B).max())
+
+
+def test_batch_fp64_matches_oracle():
+    sizes = [(6, 2000), (15, 1500)]
+    data = [synth.lingam_dataset(p, n, 0.4, seed=60 + k).X for k, (p, n) in enumerate(sizes)]
+    res = lingam.fit_batch([_dev(X, torch.float64) for X in data], precision="fp64")
+    assert res.status == 0
+    for X, o, B in zip(data, res.orders, res.Bs):
+        o_order, o_B, o_S = oracle.fit(X)
+        roots, margins = _oracle_margins(o_S)
+        # FP64 path: scores within 1e-10 relative, so every margin above 1e-9 resolves
+        for it in range(len(o) - 1):
+            if margins[it] > 1e-9 * max(1.0, roots[it]):
+                assert o[it] == o_order[it]
+            else:
+                break
+        else:
+            assert np.abs(B - o_B).max() <= 1e-10 * max(1.0, np.abs(o_B).max())
+
+
+def test_bootstrap_matches_gathered_single_fits():
+    d = synth.lingam_dataset(20, 1500, 0.2, seed=8)
+    X = d.X.astype(np.float32)
+    idx = synth.bootstrap_indices(1500, 8, seed=3)
+    assert idx.min() >= 0 and idx.max() < 1500
+    res = lingam.fit_bootstrap(_dev(X), idx, precision="mixed")
+    assert res.status == 0 and np.all(res.statuses == 0)
+    for b in range(8):
+        Xb = np.ascontiguousarray(X[:, idx[b]])
+        single, roots, margins = _single(_dev(Xb))
+        k = _agree_until_unresolved(res.orders[b], single.order, roots, margins)
+        print(f"bootstrap {b}: order equals the gathered single fit on {k} of 20 iterations")
+    # two resamples against the oracle on the gathered data
+    for b in (0, 5):
+        Xb = X[:, idx[b]].astype(np.float64)
+        o_order, o_B, o_S = oracle.fit(Xb)
+        roots, margins = _oracle_margins(o_S)
+        _agree_until_unresolved(res.orders[b], o_order, roots, margins)
+    # host indices and device indices give the same result
+    res2 = lingam.fit_bootstrap(_dev(X), torch.tensor(idx, device="cuda"), precision="mixed")
+    assert all(np.array_equal(a, b) for a, b in zip(res.orders, res2.orders))
+
+
+def test_batch_degenerate_member_does_not_stop_the_others():
+    ds = [synth.lingam_dataset(10, 800, 0.3, seed=70 + k).X.astype(np.float32) for k in range(3)]
+    ds[1][4] = 2.5   # a constant row
+    res = lingam.fit_batch([_dev(X) for X in ds], precision="mixed")
+    assert res.status == lingam.LINGAM_EDEGENERATE
+    assert list(res.statuses) == [0, lingam.LINGAM_EDEGENERATE, 0]
+    for k in (0, 2):
+        single, roots, margins = _single(_dev(ds[k]))
+        assert _agree_until_unresolved(res.orders[k], single.order, roots, margins) > 0
+
+
+def test_batch_graph_replay_is_identical():
+    ds = synth.uneven_batch(5, seed=9)
+    Xs = [_dev(d.X[:, :2000].astype(np.float32)) for d in ds]
+    ws = lingam.batch_workspace([X.shape[0] for X in Xs], [X.shape[1] for X in Xs])
+    runs = [lingam.fit_batch(Xs, precision="mixed", workspace=ws) for _ in range(3)]   # eager, capture, replay
+    for r in runs[1:]:
+        assert r.status == 0
+        assert all(np.array_equal(a, b) for a, b in zip(runs[0].orders, r.orders))
+        assert all(np.array_equal(a, b) for a, b in zip(runs[0].Bs, r.Bs))
+    # new data of the same shapes through the replayed graph
+    ds2 = synth.uneven_batch(5, seed=9)
+    Xs2 = [_dev(np.ascontiguousarray(d.X[:, :2000][::-1]).astype(np.float32)) for d in ds2]
+    r2 = lingam.fit_batch(Xs2, precision="mixed", workspace=ws)
+    for X, o in zip(Xs2, r2.orders):
+        single, roots, margins = _single(X)
+        _agree_until_unresolved(o, single.order, roots, margins)
+
+
+def test_batched_workload_full_size():
+    """256 bootstrap resamples of one p=50, n=2000 dataset and 64 uneven datasets
+    (p in 20..120, n in 500..8000), mixed path: every problem succeeds and sampled
+    problems agree with their single fits."""
+    d = synth.lingam_dataset(50, 2000, 4.0 / 49.0, seed=5)
+    X = d.X.astype(np.float32)
+    idx = synth.bootstrap_indices(2000, 256, seed=6)
+    rb = lingam.fit_bootstrap(_dev(X), idx, precision="mixed")
+    assert rb.status == 0 and np.all(rb.statuses == 0)
+    for b in (0, 97, 255):
+        single, roots, margins = _single(_dev(np.ascontiguousarray(X[:, idx[b]])))
+        k = _agree_until_unresolved(rb.orders[b], single.order, roots, margins)
+        print(f"bootstrap resample {b}: order equals the single fit on {k} of 50 iterations")
+    ds = synth.uneven_batch(64, seed=7)
+    Xs = [_dev(dd.X.astype(np.float32)) for dd in ds]
+    ru = lingam.fit_batch(Xs, precision="mixed")
+    assert ru.status == 0 and np.all(ru.statuses == 0)
+    for k in (0, 31, 63):
+        single, roots, margins = _single(Xs[k])
+        j = _agree_until_unresolved(ru.orders[k], single.order, roots, margins)
+        print(f"uneven dataset {k} (p={Xs[k].shape[0]}): order equals the single fit on {j} iterations")

@@ -252,17 +252,6 @@ def test_degenerate_inputs_are_reported(precision):
     assert e.value.status == lingam.LINGAM_EINVAL
 
 
-def test_batch_matches_single_fits():
-    ds = synth.uneven_batch(3, seed=4)
-    Xs = [_dev(d.X[:, : min(d.X.shape[1], 3000)].astype(np.float32), torch.float32) for d in ds]
-    st, status, orders, Bs = lingam.fit_batch(Xs, precision="mixed")
-    assert st == 0 and np.all(status == 0)
-    for X, o, B in zip(Xs, orders, Bs):
-        single = lingam.fit(X, precision="mixed")
-        assert np.array_equal(single.order, o)
-        assert np.array_equal(single.B, B)
-
-
 # ---------------------------------------------------------------- full size, sampled outputs
 
 def test_full_size_sampled_scores():
