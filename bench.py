@@ -180,6 +180,70 @@ def run_reference(args, rank: int, world: int):
 
 
 # ------------------------------------------------------------------ GPU leg
+def batched_workload(lingam, synth, torch, dev, stream, reps: int = 5) -> dict:
+    """The batched configuration: 256 bootstrap resamples of one p=50, n=2000 dataset
+    and 64 datasets with p in 20..120, n in 500..8000 (FP32, mixed path), each set one
+    library call; inputs resident on the device; after two calls (eager, graph capture)
+    the replayed graph is timed with CUDA events.  Next to it, sequential single fits of
+    16 members of each set (one workspace per shape reused), scaled to the whole set."""
+    import ctypes
+    d = synth.lingam_dataset(50, 2000, 4.0 / 49.0, seed=5)
+    X = torch.tensor(d.X.astype(np.float32), device=dev)
+    idx = torch.tensor(synth.bootstrap_indices(2000, 256, seed=6), device=dev)
+    ds = synth.uneven_batch(64, seed=7)
+    Xs = [torch.tensor(dd.X.astype(np.float32), device=dev) for dd in ds]
+    o, _ = lingam.make_opts()
+    wsb = lingam.alloc_workspace(lingam.load().lingam_workspace_size_bootstrap(50, 2000, 256, ctypes.byref(o)),
+                                 device=dev)
+    wsu = lingam.batch_workspace([x.shape[0] for x in Xs], [x.shape[1] for x in Xs])
+
+    def timed(fn):
+        out = []
+        for _ in range(2):
+            fn()
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            assert r.status == 0
+            out.append(e0.elapsed_time(e1))
+        return float(np.median(out))
+
+    t_boot = timed(lambda: lingam.fit_bootstrap(X, idx, workspace=wsb))
+    t_unev = timed(lambda: lingam.fit_batch(Xs, workspace=wsu))
+    # sequential single fits of 16 members of each set
+    Xb = [X[:, idx[b].long()].contiguous() for b in range(16)]
+    ws1 = lingam.alloc_workspace(lingam.workspace_size(50, 2000), device=dev)
+    for x in Xb[:2]:
+        lingam.fit(x, workspace=ws1)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for x in Xb:
+        lingam.fit(x, workspace=ws1)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    seq_boot = e0.elapsed_time(e1) / 16 * 256
+    wsm = lingam.alloc_workspace(max(lingam.workspace_size(x.shape[0], x.shape[1]) for x in Xs[:16]), device=dev)
+    lingam.fit(Xs[0], workspace=wsm)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for x in Xs[:16]:
+        lingam.fit(x, workspace=wsm)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    seq_unev = e0.elapsed_time(e1) / 16 * 64
+    return {"workload": "256 bootstrap resamples of p=50, n=2000 + 64 datasets p in 20..120, n in 500..8000",
+            "bootstrap_256_ms": t_boot, "uneven_64_ms": t_unev,
+            "sequential_single_fits_estimate_ms": {"bootstrap_256": seq_boot, "uneven_64": seq_unev},
+            "speedup_vs_sequential": {"bootstrap_256": seq_boot / t_boot, "uneven_64": seq_unev / t_unev},
+            "timing": "median of 5 graph replays, CUDA events; inputs on the device"}
+
+
 def run_ours(args, rank: int, world: int):
     import torch
     import __graft_entry__ as entry
@@ -300,6 +364,9 @@ def run_ours(args, rank: int, world: int):
                              "same_roots": bool(np.array_equal(rm.order[:k], r64.order[:k]))}
         del ws64
 
+    if world == 1 and not args.no_batch:
+        line["batched"] = batched_workload(lingam, synth, torch, dev, stream)
+
     if world == 1 and rank == 0 and not args.no_cpu:
         X64 = d.X.astype(np.float32).astype(np.float64)
         rate, dt, m, cores = oracle_rate(X64, args.cpu_seconds)
@@ -323,6 +390,7 @@ def main():
     ap.add_argument("--fp64-iters", type=int, default=5)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
     ap.add_argument("--max-iters", type=int, default=0, help="order only the first k iterations (profiling)")
