@@ -61,9 +61,9 @@ typedef struct {
     int input_dtype;         /* element type of X: LINGAM_F32 or LINGAM_F64 */
     int prune;               /* 1 = threshold pruning (Sec. III-B), 0 = compare every pair */
     int reuse;               /* 1 = one evaluation per unordered pair (Sec. III-A), 0 = every ordered pair */
-    int tile_i;              /* pair-tile rows of the mixed path: 32 or 64; 0 = lingam_tile_rows(p, n)
-                                (the autotuner's table); ignored by the FP64 path (32 rows) */
-    int tile_j;              /* reserved, must be 0 or 32 (tiles have 32 columns) */
+    int tile_i, tile_j;      /* pair-tile shape of the mixed path, rows x columns: 64 x 32, 32 x 32 or
+                                64 x 16 (a zero in one takes 64 rows or 32 columns); both 0 = the
+                                autotuner's table (lingam_tile_rows/_cols).  The FP64 path uses 32 x 32. */
     int split_n;             /* sample-axis split override; 0 = autotuned */
     double timeout_s;        /* bound on any device-side wait; <= 0 means 10 s */
     void* stream;            /* cudaStream_t to run on; NULL = the legacy default stream */
@@ -140,24 +140,28 @@ int lingam_covariance(const void* X, long long p, long long n, double* Sigma, vo
 
 /*
  * Pair-tile autotuner (the paper has no counterpart: its GPU design has one tile shape).
- * The mixed path evaluates pairs in tiles of 64 or 32 rows (variables) by 32 columns;
- * which is faster depends on how many variables remain and on n.  The library keeps a
+ * The mixed path evaluates pairs in tiles of rows x columns variables: 64 x 32 (512
+ * threads), 32 x 32 or 64 x 16 (256 threads, two CTAs per SM).  The columns of a tile are
+ * the candidates a wave completes, so 16-column tiles prune more finely (fewer pairs, more
+ * waves).  Which shape is faster depends on p, n and the data.  The library keeps a
  * process-wide table of the choice per size bucket (ceil(log2 p), ceil(log2 n)); a
- * bucket never measured uses 64-row tiles.
+ * bucket never measured uses 64 x 32.
  *
- * lingam_tile_rows   -- the tile rows lingam_fit uses for a p x n problem when
- *                       opts->tile_i is 0 (opts->tile_i = 32 or 64 forces a shape).
+ * lingam_tile_rows, lingam_tile_cols -- the shape lingam_fit uses for a p x n problem
+ *                       when opts->tile_i and opts->tile_j are 0.
  * lingam_autotune    -- measures the ordering of X (as lingam_fit with opts, B not
- *                       fitted) once with each tile shape, records the faster one for
- *                       X's size bucket and returns it in *tile_rows; ms[0], ms[1] (if
- *                       ms is not NULL) receive the ordering times with 64 and 32 rows.
- *                       Costs two fits; the workspace is as for lingam_fit.
+ *                       fitted) once with each shape, records the fastest for X's size
+ *                       bucket and returns it in *tile_rows, *tile_cols; ms[0..2] (if
+ *                       ms is not NULL) receive the ordering times with 64 x 32, 32 x 32
+ *                       and 64 x 16 tiles.  Costs three fits; the workspace is as for
+ *                       lingam_fit.
  * lingam_autotune_reset -- forgets every measured choice.
  * The table is shared by all threads of the process (guarded by a mutex).
  */
 int lingam_tile_rows(long long p, long long n);
+int lingam_tile_cols(long long p, long long n);
 int lingam_autotune(const void* X, long long p, long long n, void* workspace, const lingam_opts* opts,
-                    int* tile_rows, double* ms);
+                    int* tile_rows, int* tile_cols, double* ms);
 void lingam_autotune_reset(void);
 
 /* Workspace for lingam_fit_batch over `count` datasets of sizes p[k] x n[k]. */

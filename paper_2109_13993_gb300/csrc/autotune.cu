@@ -1,7 +1,7 @@
-// autotune.cu -- the pair-tile autotuner: the tile rows (64 or 32) of the mixed path
-// per problem-size bucket (ceil(log2 p), ceil(log2 n)), measured by lingam_autotune on
-// the caller's data and kept in a process-wide table; buckets never measured use a
-// default rule.
+// autotune.cu -- the pair-tile autotuner: the tile shape (rows x columns: 64 x 32,
+// 32 x 32 or 64 x 16) of the mixed path per problem-size bucket (ceil(log2 p),
+// ceil(log2 n)), measured by lingam_autotune on the caller's data and kept in a
+// process-wide table; buckets never measured use a default rule.
 #include <chrono>
 #include <cstring>
 #include <map>
@@ -14,7 +14,7 @@
 namespace lingam {
 
 static std::mutex g_tune_mu;
-static std::map<std::pair<int, int>, int> g_tune;   // (p bucket, n bucket) -> tile rows
+static std::map<std::pair<int, int>, TileShape> g_tune;   // (p bucket, n bucket) -> shape
 
 static int ceil_log2(long long v) {
     int b = 0;
@@ -24,24 +24,24 @@ static int ceil_log2(long long v) {
 
 static std::pair<int, int> bucket(long long p, long long n) { return {ceil_log2(p), ceil_log2(n)}; }
 
-// Default when a bucket was never measured: 64-row tiles, measured faster than
-// 32-row tiles for single fits of p = 20 ... 1000 at n = 2000 and 10^4 on GB300
+// Default when a bucket was never measured: 64 x 32 tiles, measured faster than
+// 32 x 32 tiles for single fits of p = 20 ... 1000 at n = 2000 and 10^4 on GB300
 // (by 6 % at p = 1000 to 31 % at p = 50).
-static int default_tile_rows(long long p, long long n) {
+static TileShape default_tile_shape(long long p, long long n) {
     (void)p;
     (void)n;
-    return 64;
+    return TileShape{64, 32};
 }
 
-int autotune_tile_rows(long long p, long long n) {
+TileShape autotune_tile_shape(long long p, long long n) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(bucket(p, n));
-    return it != g_tune.end() ? it->second : default_tile_rows(p, n);
+    return it != g_tune.end() ? it->second : default_tile_shape(p, n);
 }
 
-void autotune_record(long long p, long long n, int tile_rows) {
+void autotune_record(long long p, long long n, TileShape shape) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[bucket(p, n)] = tile_rows;
+    g_tune[bucket(p, n)] = shape;
 }
 
 void autotune_clear() {

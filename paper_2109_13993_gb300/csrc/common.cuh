@@ -121,6 +121,7 @@ struct Fit {
     Ctl* ctl;
     int maxtiles;        // row tiles of a wave at most (ceil(p / kTI))
     int tile_rows;       // rows of a pair tile: 64 or 32 (mixed path), 32 (FP64 path)
+    int tile_cols;       // columns of a pair tile (= of a wave): 32, or 16 (mixed path)
     int maxsplit;        // sample splits at most
 };
 

@@ -7,7 +7,7 @@
 // Phases of an iteration:
 //   plan     (CTA 0) candidate order sigma of the remaining variables U, sorted
 //            by the previous iteration's scores (iteration 0: H(x) - H(nu), most
-//            non-Gaussian first); the first wave's columns are its first kTJ.
+//            non-Gaussian first); the first wave's columns are its first TJ.
 //   waves    repeat until no live candidate is left:
 //     compute  every CTA evaluates its share of the wave's (tile, chunk) units
 //              and writes partial sample moments;
@@ -20,7 +20,7 @@
 //            / sqrt(1 - Sigma[w,root]^2) with the new H(x_w); then the covariance
 //            downdate of Eq. CovUpdate, in FP64.
 //
-// A wave pairs up to kTJ candidate variables (the columns) with every variable
+// A wave pairs up to TJ candidate variables (the columns) with every variable
 // that has not been a column yet in this iteration (the rows; the columns come
 // first among the rows so that pairs inside the block are covered).  Each
 // unordered pair is evaluated once and its measure I(i,j) of Eq. Itest serves
@@ -59,40 +59,45 @@
 
 namespace lingam {
 
-// Pair-tile shapes: TI rows x kTJ columns, CONS threads of 2 x 2 pairs each (rows ty
+// Pair-tile shapes: TI rows x TJ columns, CONS threads of 2 x 2 pairs each (rows ty
 // and ty + TI/2, columns tx and tx + 16), sample chunks of CH staged in shared-memory
 // rows of LDS elements (padded: conflict-free 16-byte loads).  The FP32 path has two
 // shapes, chosen by the tile autotuner: 64-row tiles of 512 threads (one CTA per SM)
 // and 32-row tiles of 256 threads (two CTAs per SM, less padding waste when few
 // variables remain).
-template <class T_, int TI_, int CONS_, int CH_, int LDS_, int MINB_>
+template <class T_, int TI_, int TJ_, int CONS_, int CH_, int LDS_, int STAGES_, int MINB_>
 struct PairShape {
     using T = T_;
-    static constexpr int TI = TI_;
+    static constexpr int TI = TI_;       // tile rows
+    static constexpr int TJ = TJ_;       // tile columns = columns of a wave
     static constexpr int CONS = CONS_;
     static constexpr int CH = CH_;
     static constexpr int LDS = LDS_;
+    static constexpr int STAGES = STAGES_;   // copy-ring depth
     static constexpr int MINB = MINB_;   // CTAs per SM the launch bounds ask for
+    static_assert(CONS == (TI / 2) * (TJ / 2), "each thread evaluates 2 x 2 pairs");
+    static_assert(TJ <= kTJ, "the wave buffers hold kTJ columns");
 };
-using CfgF64 = PairShape<float, 64, 512, kChunk, kChunk + 4, 1>;      // FP32, 64-row tiles
-using CfgF32 = PairShape<float, 32, 256, kChunk, kChunk + 4, 2>;      // FP32, 32-row tiles
-using CfgD = PairShape<double, 32, 256, kChunk64, kChunk64 + 2, 1>;   // FP64 path
+using CfgF64 = PairShape<float, 64, 32, 512, kChunk, kChunk + 4, 3, 1>;      // FP32, 64 x 32 tiles
+using CfgF32 = PairShape<float, 32, 32, 256, kChunk, kChunk + 4, 3, 2>;      // FP32, 32 x 32 tiles
+using CfgF16 = PairShape<float, 64, 16, 256, kChunk, kChunk + 4, 2, 2>;      // FP32, 64 x 16 tiles
+using CfgD = PairShape<double, 32, 32, 256, kChunk64, kChunk64 + 2, 3, 1>;   // FP64 path
 
 constexpr int kSortMax = 8192;   // candidate sort in shared memory up to this many variables
 
 template <class Cfg>
 __host__ __device__ constexpr size_t stage_elems() {
-    return size_t(Cfg::TI + kTJ) * Cfg::LDS;
+    return size_t(Cfg::TI + Cfg::TJ) * Cfg::LDS;
 }
 template <class Cfg>
 __host__ __device__ constexpr size_t ring_bytes() {
-    return size_t(kStages) * stage_elems<Cfg>() * sizeof(typename Cfg::T);
+    return size_t(Cfg::STAGES) * stage_elems<Cfg>() * sizeof(typename Cfg::T);
 }
 template <class Cfg>
 size_t iter_smem_bytes() {
     const size_t ring = ring_bytes<Cfg>();
     const size_t sort = size_t(kSortMax) * sizeof(unsigned long long);
-    return (ring > sort ? ring : sort) + kStages * sizeof(uint64_t);
+    return (ring > sort ? ring : sort) + kStages * sizeof(uint64_t);   // barriers for up to kStages
 }
 
 // FP32 residuals carry the scale kScale: with u' = kScale*u,
@@ -270,7 +275,7 @@ __device__ __forceinline__ int cta_of_unit(long long v, long long U, long long G
 }
 
 // ------------------------------------------------------------------ plan (CTA 0)
-template <int NTH, int TI>
+template <int NTH, int TI, int TJ>
 __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* smem, int* red) {
     Ctl* ctl = f.ctl;
     const int p = f.p, tid = threadIdx.x;
@@ -372,7 +377,7 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
             ctl->ncol = ctl->nrow = ctl->ntiles = 0;
         } else {
             ctl->done = 0;
-            const int nc = r < kTJ ? r : kTJ;
+            const int nc = r < TJ ? r : TJ;
             for (int c = 0; c < nc; ++c) f.cols[c] = f.sigma[c];
             ctl->ncol = nc;
             ctl->nrow = r;
@@ -383,7 +388,7 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
 
 // ------------------------------------------------------------------ wave finalisation
 // Run by one CTA (the one that merged the wave's last tile).
-template <int NTH, int TI>
+template <int NTH, int TI, int TJ>
 __device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
     Ctl* ctl = f.ctl;
     volatile Ctl* vc = ctl;
@@ -407,12 +412,12 @@ __device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
     __shared__ double s_col[32 * 33];
     double tot = 0.0;
     for (int t0 = 0; t0 < ntiles; t0 += 32) {
-        for (int k = tid; k < 32 * kTJ; k += NTH) {
-            const int t = t0 + k / kTJ;
-            s_col[(k / kTJ) * 33 + (k % kTJ)] = t < ntiles ? ld2(f.colsum + t * kTJ + (k % kTJ)) : 0.0;
+        for (int k = tid; k < 32 * TJ; k += NTH) {
+            const int t = t0 + k / TJ;
+            s_col[(k / TJ) * 33 + (k % TJ)] = t < ntiles ? ld2(f.colsum + t * TJ + (k % TJ)) : 0.0;
         }
         __syncthreads();
-        if (tid < kTJ)
+        if (tid < TJ)
             for (int j = 0; j < 32 && t0 + j < ntiles; ++j) tot += s_col[j * 33 + tid];
         __syncthreads();
     }
@@ -450,7 +455,7 @@ __device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
     const double best = vc->best;
 
     // 4. one pass over the candidates: prune (partial score above the threshold), pick
-    //    the next columns (the first kTJ live un-columned variables in candidate order)
+    //    the next columns (the first TJ live un-columned variables in candidate order)
     //    and list the next rows (every other row-eligible variable: un-columned ones with
     //    reuse, all remaining ones without), both in candidate order.
     // The candidates' flags and scores are fetched for all of this thread's positions
@@ -497,18 +502,18 @@ __device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
         // ranks among live and among eligible variables (a pick is live and eligible)
         scan01x2<NTH>(live, elig, red, &pl, &pe, &tl, &te);
         const int lrank = nlive + pl;
-        const bool pick = live && lrank < kTJ;
+        const bool pick = live && lrank < TJ;
         // every pick is eligible; the row rank of an eligible non-pick is the rows listed
         // so far plus the eligible variables before it in this block minus the picks among them
-        const int picked_before = min(nlive + pl, kTJ) - min(nlive, kTJ);
+        const int picked_before = min(nlive + pl, TJ) - min(nlive, TJ);
         if (pick) f.cols[lrank] = v;
         if (elig && !pick) f.scratch[nr + pe - picked_before] = v;
-        const int picks_here = min(nlive + tl, kTJ) - min(nlive, kTJ);
+        const int picks_here = min(nlive + tl, TJ) - min(nlive, TJ);
         nlive += tl;
         nr += te - picks_here;
         __syncthreads();
     }
-    const int nc = nlive < kTJ ? nlive : kTJ;
+    const int nc = nlive < TJ ? nlive : TJ;
     __syncthreads();
     for (int k = tid; k < nc + nr; k += NTH) f.rows[k] = k < nc ? ld2(f.cols + k) : ld2(f.scratch + k - nc);
     __syncthreads();
@@ -592,8 +597,9 @@ __device__ __forceinline__ void issue_part(const Fit& f, typename Cfg::T* stage,
                                            int ncol, int& ctile, int& cvar) {
     using T = typename Cfg::T;
     constexpr int CH = Cfg::CH, LDS = Cfg::LDS, TI = Cfg::TI, NW = Cfg::CONS / 32;
-    constexpr int SPW = (TI + kTJ) / NW;
-    static_assert(SPW * NW == TI + kTJ && SPW <= 32, "copy rows must split evenly over the warps");
+    constexpr int TJ = Cfg::TJ;
+    constexpr int SPW = (TI + TJ) / NW;
+    static_assert(SPW * NW == TI + TJ && SPW <= 32, "copy rows must split evenly over the warps");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int t = int(unit / nch), c = int(unit % nch);
     const int slot = w * SPW + lane;
@@ -610,7 +616,7 @@ __device__ __forceinline__ void issue_part(const Fit& f, typename Cfg::T* stage,
         }
         cvar = v;
     }
-    if (threadIdx.x == 0) mbar_expect_tx(bar, uint32_t(TI + kTJ) * CH * sizeof(T));
+    if (threadIdx.x == 0) mbar_expect_tx(bar, uint32_t(TI + TJ) * CH * sizeof(T));
     if (lane < SPW) {
         fence_proxy_async();
         const T* xt = static_cast<const T*>(f.xt);
@@ -667,14 +673,15 @@ __device__ __noinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wave& 
     const int base = chunk_base;   // ring position of this wave's first chunk
 
     int ctile = -1, cvar = -1;   // this thread's copy row (rows and columns changed with the wave)
-    for (int k = 0; k < min(total, kStages); ++k) {
-        const int s = (base + k) % kStages;
+    for (int k = 0; k < min(total, Cfg::STAGES); ++k) {
+        const int s = (base + k) % Cfg::STAGES;
         issue_part<Cfg>(f, ring + size_t(s) * stage_elems<Cfg>(), &full[s], c_lo + k, nch, nrow, ncol, ctile, cvar);
     }
-    int issued = min(total, kStages);   // chunks whose copies were issued
+    int issued = min(total, Cfg::STAGES);   // chunks whose copies were issued
 
-    const int ty = tid >> 4, tx = tid & 15;
-    const int rsl[2] = {ty, ty + TI / 2}, csl[2] = {tx, tx + 16};
+    constexpr int HJ = Cfg::TJ / 2;
+    const int ty = tid / HJ, tx = tid % HJ;
+    const int rsl[2] = {ty, ty + TI / 2}, csl[2] = {tx, tx + HJ};
     const T grp_off = T(-double(kSub) * (kLn2 + kBeta));
     T* parts = static_cast<T*>(f.partials);
     int k = 0;   // chunk index within this wave (this CTA)
@@ -720,8 +727,8 @@ __device__ __noinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wave& 
             const int tt1 = int(min(seg_end, (cg + 1) * GPC) - cg * GPC) * kSub;
             g = min(seg_end, (cg + 1) * GPC);
             const int pos = base + k;
-            const int s = pos % kStages;
-            const bool okw = mbar_wait_or_abort(&full[s], (pos / kStages) & 1, gctl, tmo, &sh.abort);
+            const int s = pos % Cfg::STAGES;
+            const bool okw = mbar_wait_or_abort(&full[s], (pos / Cfg::STAGES) & 1, gctl, tmo, &sh.abort);
             if (!okw) sh.abort = 1;
             const T* st = ring + size_t(s) * stage_elems<Cfg>();
             const T* R0 = st + rsl[0] * LDS;
@@ -813,15 +820,15 @@ __device__ __noinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wave& 
             }
             }
             // every warp is done with the stage (or a wait gave up: all leave together);
-            // each warp copies its rows of the chunk kStages further on into it
+            // each warp copies its rows of the chunk Cfg::STAGES further on into it
             if (__syncthreads_or(!okw)) {
                 ok = false;
                 break;
             }
-            if (k + kStages < total) {
-                issue_part<Cfg>(f, ring + size_t(s) * stage_elems<Cfg>(), &full[s], c_lo + k + kStages, nch, nrow, ncol,
+            if (k + Cfg::STAGES < total) {
+                issue_part<Cfg>(f, ring + size_t(s) * stage_elems<Cfg>(), &full[s], c_lo + k + Cfg::STAGES, nch, nrow, ncol,
                               ctile, cvar);
-                issued = k + kStages + 1;
+                issued = k + Cfg::STAGES + 1;
             }
         }
         if (__syncthreads_or(!ok)) {
@@ -831,7 +838,7 @@ __device__ __noinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wave& 
                 for (int k2 = k; k2 < issued; ++k2) {
                     const int pos = base + k2;
                     const unsigned long long t0 = global_ns();
-                    while (!mbar_try_wait(&full[pos % kStages], (pos / kStages) & 1) &&
+                    while (!mbar_try_wait(&full[pos % Cfg::STAGES], (pos / Cfg::STAGES) & 1) &&
                            global_ns() - t0 < 2000000000ull) {
                     }
                 }
@@ -866,7 +873,7 @@ template <class Cfg>
 __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span& sp, int it, IterShared& sh,
                                         typename Cfg::T* scratch, int item) {
     using T = typename Cfg::T;
-    constexpr int TI = Cfg::TI, CONS = Cfg::CONS;
+    constexpr int TI = Cfg::TI, TJ = Cfg::TJ, CONS = Cfg::CONS;
     constexpr int NW = CONS / 32;
     constexpr int PARTS = CONS / 64;            // items per tile
     constexpr bool kF32 = std::is_same<T, float>::value;
@@ -911,7 +918,7 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
                 }
             // pair tid of the item = pair (tid & 3) of compute thread part * 64 + tid / 4
             const int ct = part * 64 + (tid >> 2), q = tid & 3;
-            const int e_loc = (ct >> 4) + (q >> 1) * (TI / 2), cc = (ct & 15) + (q & 1) * 16;
+            const int e_loc = ct / (TJ / 2) + (q >> 1) * (TI / 2), cc = ct % (TJ / 2) + (q & 1) * (TJ / 2);
             const int e = t * TI + e_loc;
             const int vi = e < nrow ? ld2(f.rows + e) : -1;
             const int vj = cc < ncol ? ld2(f.cols + cc) : -1;
@@ -931,7 +938,7 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
                 }
                 if (!isfinite(double(I))) set_status(ctl, LINGAM_EDEGENERATE);
             }
-            ibuf[(size_t(t) * TI + e_loc) * kTJ + cc] = I;
+            ibuf[(size_t(t) * TI + e_loc) * TJ + cc] = I;
         }
         __threadfence();
         __syncthreads();
@@ -939,10 +946,10 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
         __syncthreads();
         if (sh.flag) {
             // 3. the tile's last item: per-row and per-column contributions in FP64, from the
-            //    tile's I staged in shared memory (row stride kTJ + 1)
+            //    tile's I staged in shared memory (row stride TJ + 1)
             __threadfence();
-            const T* It = ibuf + size_t(t) * TI * kTJ;
-            for (int k = tid; k < TI * kTJ; k += CONS) scratch[(k / kTJ) * (kTJ + 1) + (k % kTJ)] = __ldcg(It + k);
+            const T* It = ibuf + size_t(t) * TI * TJ;
+            for (int k = tid; k < TI * TJ; k += CONS) scratch[(k / TJ) * (TJ + 1) + (k % TJ)] = __ldcg(It + k);
             __syncthreads();
             if constexpr (kF32) {
                 // squares summed exactly enough (float-float) that a variable's score does not
@@ -950,31 +957,31 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
                 if (tid < TI) {
                     const int e = t * TI + tid;
                     FF acc;
-                    for (int cc = 0; cc < kTJ; ++cc) acc.add_sq(fminf(scratch[tid * (kTJ + 1) + cc], 0.f));
+                    for (int cc = 0; cc < TJ; ++cc) acc.add_sq(fminf(scratch[tid * (TJ + 1) + cc], 0.f));
                     if (e < nrow) f.rowsum[e] = acc.value();
-                } else if (tid < TI + kTJ) {
+                } else if (tid < TI + TJ) {
                     const int cc = tid - TI;
                     FF acc;
-                    for (int e = 0; e < TI; ++e) acc.add_sq(fmaxf(scratch[e * (kTJ + 1) + cc], 0.f));
-                    f.colsum[t * kTJ + cc] = acc.value();
+                    for (int e = 0; e < TI; ++e) acc.add_sq(fmaxf(scratch[e * (TJ + 1) + cc], 0.f));
+                    f.colsum[t * TJ + cc] = acc.value();
                 }
             } else {
                 if (tid < TI) {
                     const int e = t * TI + tid;
                     double s = 0.0;
-                    for (int cc = 0; cc < kTJ; ++cc) {
-                        const double m = fmin(double(scratch[tid * (kTJ + 1) + cc]), 0.0);
+                    for (int cc = 0; cc < TJ; ++cc) {
+                        const double m = fmin(double(scratch[tid * (TJ + 1) + cc]), 0.0);
                         s = fma(m, m, s);
                     }
                     if (e < nrow) f.rowsum[e] = s;
-                } else if (tid < TI + kTJ) {
+                } else if (tid < TI + TJ) {
                     const int cc = tid - TI;
                     double s = 0.0;
                     for (int e = 0; e < TI; ++e) {
-                        const double m = fmax(double(scratch[e * (kTJ + 1) + cc]), 0.0);
+                        const double m = fmax(double(scratch[e * (TJ + 1) + cc]), 0.0);
                         s = fma(m, m, s);
                     }
-                    f.colsum[t * kTJ + cc] = s;
+                    f.colsum[t * TJ + cc] = s;
                 }
             }
             if (tid == 0) f.tile_cnt[t] = 0;
@@ -984,7 +991,7 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
             __syncthreads();
             if (sh.flag) {
                 __threadfence();
-                wave_finalize<CONS, TI>(f, it, sh.red);
+                wave_finalize<CONS, TI, TJ>(f, it, sh.red);
             }
         }
         __syncthreads();
@@ -1127,13 +1134,13 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
     if (vc->status != 0) return;
     const unsigned long long tmo = vc->timeout_ns;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < Cfg::STAGES; ++s) mbar_init(&full[s], 1);
         sh.abort = 0;
         fence_barrier_init();
     }
     __syncthreads();
 
-    if (blockIdx.x == 0) plan_phase<Cfg::CONS, Cfg::TI>(f, it, smem_raw, sh.red);
+    if (blockIdx.x == 0) plan_phase<Cfg::CONS, Cfg::TI, Cfg::TJ>(f, it, smem_raw, sh.red);
     if (!grid_sync(ctl, tmo)) return;
     int chunk_base = 0;
     while (!vc->done) {
@@ -1283,7 +1290,7 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
     if (vb->status != 0) return;
     const unsigned long long tmo = vb->timeout_ns;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < Cfg::STAGES; ++s) mbar_init(&full[s], 1);
         sh.abort = 0;
         fence_barrier_init();
     }
@@ -1293,7 +1300,7 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
         // plan (a problem whose status turned bad stays done: it is not planned again)
         batch_active(fits, count, it, 0, bs);
         for (int d = blockIdx.x; d < count; d += gridDim.x)
-            if (bs.act[d]) plan_phase<CONS, TI>(fits[d], it, smem_raw, sh.red);
+            if (bs.act[d]) plan_phase<CONS, TI, Cfg::TJ>(fits[d], it, smem_raw, sh.red);
         if (!grid_sync(bctl, tmo)) return;
         for (;;) {
             long long utot;
@@ -1351,6 +1358,7 @@ static int grid_for(int nsm) {
 
 int iteration_grid(const Fit& f, int nsm) {
     if (f.precision != LINGAM_MIXED) return grid_for<CfgD>(nsm);
+    if (f.tile_cols == 16) return grid_for<CfgF16>(nsm);
     return f.tile_rows == 32 ? grid_for<CfgF32>(nsm) : grid_for<CfgF64>(nsm);
 }
 
@@ -1367,6 +1375,7 @@ static cudaError_t launch_iter(const Fit& f, int it, int grid, cudaStream_t st) 
 
 cudaError_t launch_iteration(const Fit& f, int it, int grid, cudaStream_t st) {
     if (f.precision != LINGAM_MIXED) return launch_iter<CfgD>(f, it, grid, st);
+    if (f.tile_cols == 16) return launch_iter<CfgF16>(f, it, grid, st);
     return f.tile_rows == 32 ? launch_iter<CfgF32>(f, it, grid, st) : launch_iter<CfgF64>(f, it, grid, st);
 }
 

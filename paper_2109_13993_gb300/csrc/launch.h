@@ -46,10 +46,13 @@ cudaError_t launch_fit_B(const Fit& f, cudaStream_t st);
 cudaError_t launch_fit_B_batch(const Fit* fits_dev, const int* p_host, int count, const Fit* fits_host,
                                cudaStream_t st);
 
-// Pair-tile autotuner (autotune.cu): the tile rows of the mixed path for a problem size,
-// recording a measured choice, and forgetting all of them.
-int autotune_tile_rows(long long p, long long n);
-void autotune_record(long long p, long long n, int tile_rows);
+// Pair-tile autotuner (autotune.cu): the tile shape of the mixed path for a problem
+// size, recording a measured choice, and forgetting all of them.
+struct TileShape {
+    int rows, cols;
+};
+TileShape autotune_tile_shape(long long p, long long n);
+void autotune_record(long long p, long long n, TileShape shape);
 void autotune_clear();
 
 }  // namespace lingam

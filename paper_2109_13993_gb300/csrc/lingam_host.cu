@@ -107,18 +107,18 @@ static Layout make_layout(long long p, long long n, int precision, int input_dty
     return L;
 }
 
-// Pair-tile rows of the mixed path: the caller's choice (32 or 64), else the tile
-// autotuner's choice for this problem size.
-static int choose_tile_rows(int p, int n, int tile_i) {
-    if (tile_i == 32 || tile_i == 64) return tile_i;
-    return autotune_tile_rows(p, n);
+// Pair-tile shape of the mixed path: the caller's choice (tile_i rows, tile_j columns;
+// a zero takes 64 rows or 32 columns), else the tile autotuner's choice for this size.
+static TileShape choose_tile(long long p, long long n, int tile_i, int tile_j) {
+    if (tile_i == 0 && tile_j == 0) return autotune_tile_shape(p, n);
+    return TileShape{tile_i ? tile_i : 64, tile_j ? tile_j : 32};
 }
 
 static bool valid_opts(const lingam_opts& o) {
     return (o.precision == LINGAM_MIXED || o.precision == LINGAM_FP64) &&
            (o.input_dtype == LINGAM_F32 || o.input_dtype == LINGAM_F64) && (o.prune == 0 || o.prune == 1) &&
            (o.reuse == 0 || o.reuse == 1) && o.split_n >= 0 && (o.tile_i == 0 || o.tile_i == 32 || o.tile_i == 64) &&
-           (o.tile_j == 0 || o.tile_j == 32);
+           (o.tile_j == 0 || o.tile_j == 16 || o.tile_j == 32) && !(o.tile_i == 32 && o.tile_j == 16);
 }
 
 static bool is_device_ptr(const void* ptr) {
@@ -172,7 +172,9 @@ static Fit make_fit(char* base, const Layout& L, int p, int n, const lingam_opts
     f.ctl = reinterpret_cast<Ctl*>(base + L.off_ctl);
     f.maxtiles = L.maxtiles;
     f.maxsplit = L.maxsplit;
-    f.tile_rows = o.precision == LINGAM_MIXED ? choose_tile_rows(p, n, o.tile_i) : 32;
+    const TileShape ts = o.precision == LINGAM_MIXED ? choose_tile(p, n, o.tile_i, o.tile_j) : TileShape{32, 32};
+    f.tile_rows = ts.rows;
+    f.tile_cols = ts.cols;
     return f;
 }
 
@@ -545,6 +547,7 @@ static int fit_many(std::vector<BatchItem>& items, void* workspace, const lingam
         Fit f = make_fit(base, L, int(it.p), int(it.n), o, it.rep && it.rep->scores);
         f.ctl = reinterpret_cast<Ctl*>(ws + BL.off_ctls) + k;
         f.tile_rows = o.precision == LINGAM_MIXED ? 64 : 32;   // the batch kernel's tile shape
+        f.tile_cols = 32;
         fits[size_t(k)] = f;
         SrcDesc sd;
         if (boot) {
@@ -707,35 +710,41 @@ int lingam_covariance(const void* X, long long p, long long n, double* Sigma, vo
 
 int lingam_tile_rows(long long p, long long n) {
     if (p < 1 || n < 3) return 0;
-    return autotune_tile_rows(p, n);
+    return autotune_tile_shape(p, n).rows;
+}
+
+int lingam_tile_cols(long long p, long long n) {
+    if (p < 1 || n < 3) return 0;
+    return autotune_tile_shape(p, n).cols;
 }
 
 int lingam_autotune(const void* X, long long p, long long n, void* workspace, const lingam_opts* opts,
-                    int* tile_rows, double* ms) {
+                    int* tile_rows, int* tile_cols, double* ms) {
     lingam_opts o;
     lingam_default_opts(&o);
     if (opts) o = *opts;
-    if (!tile_rows || o.precision != LINGAM_MIXED || o.forced_order) return LINGAM_EINVAL;
+    if (!tile_rows || !tile_cols || o.precision != LINGAM_MIXED || o.forced_order) return LINGAM_EINVAL;
     if (p < 1 || n < 3 || p > kMaxP) return LINGAM_EINVAL;
     std::vector<int> order(static_cast<size_t>(p));
-    const int cand[2] = {64, 32};
-    double t[2] = {0.0, 0.0};
-    for (int c = 0; c < 2; ++c) {
+    const TileShape cand[3] = {{64, 32}, {32, 32}, {64, 16}};
+    double t[3] = {0.0, 0.0, 0.0};
+    int best = 0;
+    for (int c = 0; c < 3; ++c) {
         lingam_opts oc = o;
-        oc.tile_i = cand[c];
+        oc.tile_i = cand[c].rows;
+        oc.tile_j = cand[c].cols;
         lingam_report rep;
         std::memset(&rep, 0, sizeof(rep));
         const int st = fit_one(X, p, n, order.data(), nullptr, workspace, oc, &rep);
         if (st != LINGAM_OK) return st;
         t[c] = rep.t_order_ms;
+        if (t[c] < t[best]) best = c;
     }
-    const int best = t[1] < t[0] ? 32 : 64;
-    autotune_record(p, n, best);
-    *tile_rows = best;
-    if (ms) {
-        ms[0] = t[0];
-        ms[1] = t[1];
-    }
+    autotune_record(p, n, cand[best]);
+    *tile_rows = cand[best].rows;
+    *tile_cols = cand[best].cols;
+    if (ms)
+        for (int c = 0; c < 3; ++c) ms[c] = t[c];
     return LINGAM_OK;
 }
 

@@ -91,8 +91,10 @@ def load():
     L.lingam_covariance.restype = ctypes.c_int
     L.lingam_tile_rows.argtypes = [ctypes.c_longlong, ctypes.c_longlong]
     L.lingam_tile_rows.restype = ctypes.c_int
+    L.lingam_tile_cols.argtypes = [ctypes.c_longlong, ctypes.c_longlong]
+    L.lingam_tile_cols.restype = ctypes.c_int
     L.lingam_autotune.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p,
-                                  ctypes.POINTER(Opts), _c_int_p, _c_dbl_p]
+                                  ctypes.POINTER(Opts), _c_int_p, _c_int_p, _c_dbl_p]
     L.lingam_autotune.restype = ctypes.c_int
     L.lingam_autotune_reset.argtypes = []
     L.lingam_autotune_reset.restype = None
@@ -114,7 +116,7 @@ def status_string(status: int) -> str:
 
 def make_opts(precision: str = "mixed", input_dtype=np.float32, prune: bool = True, reuse: bool = True,
               split_n: int = 0, timeout_s: float = 10.0, stream=None, forced_order=None, max_iters: int = 0,
-              timing: bool = False, tile_i: int = 0) -> tuple[Opts, object]:
+              timing: bool = False, tile_i: int = 0, tile_j: int = 0) -> tuple[Opts, object]:
     o = Opts()
     load().lingam_default_opts(ctypes.byref(o))
     o.precision = {"mixed": LINGAM_MIXED, "fp64": LINGAM_FP64}[precision]
@@ -127,6 +129,7 @@ def make_opts(precision: str = "mixed", input_dtype=np.float32, prune: bool = Tr
     o.max_iters = int(max_iters)
     o.timing = int(bool(timing))
     o.tile_i = int(tile_i)
+    o.tile_j = int(tile_j)
     keep = None
     if forced_order is not None:
         keep = np.ascontiguousarray(forced_order, dtype=np.int32)
@@ -190,7 +193,7 @@ def _data_ptr(X):
 def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, forced_order=None,
         want_scores: bool = False, want_B: bool = True, split_n: int = 0, timeout_s: float = 10.0,
         stream=None, workspace=None, max_iters: int = 0, timing: bool = False, out=None,
-        tile_i: int = 0) -> FitResult:
+        tile_i: int = 0, tile_j: int = 0) -> FitResult:
     """lingam_fit on X (p x n, numpy on the host or a torch tensor on the GPU)."""
     L = load()
     ptr, p, n, dt, keep = _data_ptr(X)
@@ -198,7 +201,7 @@ def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, for
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     o, keep_forced = make_opts(precision, dt, prune, reuse, split_n, timeout_s, stream, forced_order, max_iters,
-                               timing, tile_i)
+                               timing, tile_i, tile_j)
     need = int(L.lingam_workspace_size(p, n, ctypes.byref(o)))
     if need == 0:
         raise LingamError(LINGAM_EINVAL, "invalid sizes or options")
@@ -265,9 +268,15 @@ def tile_rows(p: int, n: int) -> int:
     return int(load().lingam_tile_rows(p, n))
 
 
+def tile_shape(p: int, n: int) -> tuple[int, int]:
+    """(rows, columns) of the pair tiles the mixed path uses for a p x n problem."""
+    L = load()
+    return int(L.lingam_tile_rows(p, n)), int(L.lingam_tile_cols(p, n))
+
+
 def autotune(X, stream=None, workspace=None):
-    """lingam_autotune on X: times the ordering with 64- and 32-row pair tiles, records
-    the faster for X's size bucket; returns (tile_rows, {64: ms, 32: ms})."""
+    """lingam_autotune on X: times the ordering with 64x32, 32x32 and 64x16 pair tiles,
+    records the fastest for X's size bucket; returns ((rows, cols), {shape: ms})."""
     L = load()
     ptr, p, n, dt, keep = _data_ptr(X)
     if stream is None:
@@ -276,14 +285,14 @@ def autotune(X, stream=None, workspace=None):
     need = int(L.lingam_workspace_size(p, n, ctypes.byref(o)))
     if workspace is None or workspace.numel() < need:
         workspace = alloc_workspace(need)
-    tr = ctypes.c_int(0)
-    ms = (ctypes.c_double * 2)()
+    tr, tc = ctypes.c_int(0), ctypes.c_int(0)
+    ms = (ctypes.c_double * 3)()
     st = L.lingam_autotune(ctypes.c_void_p(ptr), p, n, ctypes.c_void_p(workspace.data_ptr()), ctypes.byref(o),
-                           ctypes.byref(tr), ms)
+                           ctypes.byref(tr), ctypes.byref(tc), ms)
     del keep
     if st != LINGAM_OK:
         raise LingamError(st, status_string(st))
-    return int(tr.value), {64: float(ms[0]), 32: float(ms[1])}
+    return (int(tr.value), int(tc.value)), {(64, 32): float(ms[0]), (32, 32): float(ms[1]), (64, 16): float(ms[2])}
 
 
 def autotune_reset():

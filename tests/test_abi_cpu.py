@@ -68,10 +68,14 @@ def test_tile_rows_default_rule(lib):
     assert lingam.tile_rows(20, 2000) == 64
     assert lingam.tile_rows(1000, 10000) == 64
     assert lingam.tile_rows(0, 100) == 0
+    assert lingam.tile_shape(1000, 10000) == (64, 32)
     o, _ = lingam.make_opts()
-    for bad in (16, 48, 128):
-        o.tile_i = bad
+    for ti, tj in ((16, 0), (48, 0), (128, 0), (0, 8), (0, 64), (32, 16)):
+        o.tile_i, o.tile_j = ti, tj
         assert lib.lingam_workspace_size(10, 100, ctypes.byref(o)) == 0
+    for ti, tj in ((64, 32), (32, 32), (64, 16), (0, 16), (32, 0)):
+        o.tile_i, o.tile_j = ti, tj
+        assert lib.lingam_workspace_size(10, 100, ctypes.byref(o)) > 0
 
 
 def test_batch_and_bootstrap_workspace_sizes(lib):

@@ -132,21 +132,22 @@ def test_fp64_path_matches_oracle(seed):
 
 # ---------------------------------------------------------------- mixed path vs oracle, 1e-4
 
-@pytest.mark.parametrize("name,seed,tile_i", [("p20_n2000", 1, 64), ("p20_n2000", 2, 32), ("p100_n10000", 1, 64),
-                                            ("p100_n10000", 1, 32)])
-def test_mixed_path_matches_oracle(name, seed, tile_i):
+@pytest.mark.parametrize("name,seed,tile_i,tile_j", [("p20_n2000", 1, 64, 32), ("p20_n2000", 2, 32, 32),
+                                                   ("p20_n2000", 1, 64, 16), ("p100_n10000", 1, 64, 32),
+                                                   ("p100_n10000", 1, 32, 32), ("p100_n10000", 1, 64, 16)])
+def test_mixed_path_matches_oracle(name, seed, tile_i, tile_j):
     d = synth.workload(name, seed=seed)
     X32 = d.X.astype(np.float32)
     o_order, o_B, o_S = oracle.fit(X32.astype(np.float64))
     res = lingam.fit(_dev(X32, torch.float32), precision="mixed", prune=False, forced_order=o_order,
-                     want_scores=True, tile_i=tile_i)
+                     want_scores=True, tile_i=tile_i, tile_j=tile_j)
     tau = _check_scores(res.scores, o_S, rtol=0.0, atol=1e-4)
     resolved = _check_argmin_resolved(res.scores, o_S, tau)
     tau_v, kappa = _per_score_bound(res.scores, o_S, kappa_max=1e-5)
     resolved_v = _check_argmin_resolved_per_score(res.scores, o_S, tau_v)
-    free = lingam.fit(_dev(X32, torch.float32), precision="mixed", tile_i=tile_i)
+    free = lingam.fit(_dev(X32, torch.float32), precision="mixed", tile_i=tile_i, tile_j=tile_j)
     upto = _check_free_run(free.order, o_order, o_S, tau)
-    print(f"{name}/{seed} tile {tile_i}: max score error {tau.max():.2e}; {resolved} of {len(o_order)} iterations "
+    print(f"{name}/{seed} tile {tile_i}x{tile_j}: max score error {tau.max():.2e}; {resolved} of {len(o_order)} iterations "
           f"resolved by the per-iteration bound, {resolved_v} by the per-score bound (kappa {kappa:.1e}); "
           f"free-run order identical on the first {upto}")
     assert sorted(free.order.tolist()) == list(range(len(o_order)))
@@ -155,11 +156,6 @@ def test_mixed_path_matches_oracle(name, seed, tile_i):
 
 
 # ---------------------------------------------------------------- threshold pruning is exact
-
-def pr_tile(X):
-    """Tile rows the library picks for X by default (the autotuner's choice)."""
-    import ctypes
-    return lingam.tile_rows(X.shape[0], X.shape[1])
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_pruning_and_reuse_do_not_change_the_result(precision):
@@ -173,9 +169,10 @@ def test_pruning_and_reuse_do_not_change_the_result(precision):
         # the other tile shape groups each pair's samples differently: the same order, and
         # scores equal up to the FP32 rounding of I (about 1e-6 absolute on Eq. HApp values
         # near 1.4), which moves S = sum_j I_j^2 by at most 2e-6 sqrt(m S) <= 2e-8 here
-        other = lingam.fit(X, precision=precision, prune=True, tile_i=32 if pr_tile(X) == 64 else 64)
-        assert np.array_equal(other.order, pr.order)
-        assert np.allclose(other.root_score, pr.root_score, rtol=1e-4, atol=2e-8)
+        for ti, tj in ((64, 32), (32, 32), (64, 16)):
+            other = lingam.fit(X, precision=precision, prune=True, tile_i=ti, tile_j=tj)
+            assert np.array_equal(other.order, pr.order)
+            assert np.allclose(other.root_score, pr.root_score, rtol=1e-4, atol=2e-8)
     # same scores up to the FP32 rounding of how a pair's samples were split across CTAs
     assert np.allclose(pr.root_score, full.root_score, rtol=1e-4, atol=1e-10)
     assert full.pairs_total == full.pairs_unpruned
@@ -280,9 +277,9 @@ def test_autotuner_records_its_choice():
     X = _dev(d.X.astype(np.float32), torch.float32)
     lingam.autotune_reset()
     chosen, ms = lingam.autotune(X)
-    assert chosen in (32, 64) and ms[64] > 0 and ms[32] > 0
-    assert chosen == (32 if ms[32] < ms[64] else 64)
-    assert lingam.tile_rows(100, 10000) == chosen
-    print(f"autotune p=100 n=1e4: 64-row {ms[64]:.2f} ms, 32-row {ms[32]:.2f} ms -> {chosen}")
+    assert chosen in ms and all(v > 0 for v in ms.values())
+    assert chosen == min(ms, key=ms.get)
+    assert lingam.tile_shape(100, 10000) == chosen
+    print(f"autotune p=100 n=1e4: {ms} -> {chosen}")
     lingam.autotune_reset()
-    assert lingam.tile_rows(100, 10000) == 64
+    assert lingam.tile_shape(100, 10000) == (64, 32)
