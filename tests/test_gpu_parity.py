@@ -251,6 +251,42 @@ def test_degenerate_inputs_are_reported(precision):
 
 # ---------------------------------------------------------------- full size, sampled outputs
 
+def test_p300_denser_dag_mixed_vs_fp64_and_oracle():
+    """p = 300, n = 5000 with edge probability 6/299 (denser DAG): the mixed path
+    (tensor-core covariance, FP32 pair measure, FP64 downdates) against the FP64 GPU
+    path on every score of every iteration (both unpruned, both in the FP64 path's
+    order), sampled scores against the oracle at iterations 0 and 150, and B of both
+    paths against the oracle's least squares on the same order."""
+    d = synth.workload("p300_n5000", seed=1)
+    X32 = d.X.astype(np.float32)
+    X64 = X32.astype(np.float64)
+    f64 = lingam.fit(_dev(X64, torch.float64), precision="fp64", prune=False, want_scores=True)
+    mix = lingam.fit(_dev(X32, torch.float32), precision="mixed", prune=False, forced_order=f64.order,
+                     want_scores=True)
+    m = ~np.isnan(f64.scores)
+    assert np.array_equal(m, ~np.isnan(mix.scores))
+    dS = np.abs(mix.scores[m] - f64.scores[m])
+    assert dS.max() <= 1e-4
+    free = lingam.fit(_dev(X32, torch.float32), precision="mixed")
+    same = int(np.argmax(free.order != f64.order)) if np.any(free.order != f64.order) else 300
+    for it in (0, 150):
+        vs = np.nonzero(~np.isnan(f64.scores[it]))[0][:: 10 if it == 0 else 5]
+        ora = oracle.variable_scores(X64, f64.order[:it], vs)
+        d64 = np.abs(f64.scores[it, vs] - ora)
+        assert np.all(d64 <= 1e-10 * np.abs(ora) + 1e-14)
+        e64 = (d64 / np.maximum(np.abs(ora), 1e-14)).max()
+        emx = np.abs(mix.scores[it, vs] - ora)
+        assert emx.max() <= 1e-4
+    oB = oracle.fit_B(X64, f64.order)
+    scale = max(1.0, np.abs(oB).max())
+    eB64 = np.abs(f64.B - oB).max() / scale
+    eBmx = np.abs(mix.B - oB).max() / scale
+    assert eB64 <= 1e-10 and eBmx <= 1e-4
+    print(f"p=300 n=5000 q=6/299: max |S_mixed - S_fp64| {dS.max():.2e}; free-run mixed order equals the "
+          f"FP64 path's on the first {same} iterations; B error (relative to max |B|) FP64 {eB64:.1e}, "
+          f"mixed {eBmx:.1e}; oracle sample errors FP64 {e64:.1e} (rel), mixed {emx.max():.1e}")
+
+
 def test_full_size_sampled_scores():
     """p = 1000, n = 10^4 in the configuration the benchmark times (mixed,
     pruning and reuse on): sampled complete scores against the oracle at
