@@ -97,7 +97,7 @@ template <class Cfg>
 size_t iter_smem_bytes() {
     const size_t ring = ring_bytes<Cfg>();
     const size_t sort = size_t(kSortMax) * sizeof(unsigned long long);
-    return (ring > sort ? ring : sort) + kStages * sizeof(uint64_t);   // barriers for up to kStages
+    return (ring > sort ? ring : sort) + 2 * kStages * sizeof(uint64_t);   // full and empty barriers
 }
 
 // FP32 residuals carry the scale kScale: with u' = kScale*u,
@@ -646,7 +646,8 @@ __device__ __forceinline__ Span single_span(long long U, long long Gmax) {
 
 template <class Cfg>
 __device__ __noinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wave& wv, const Span& sp,
-                                           typename Cfg::T* ring, uint64_t* full, IterShared& sh, int& chunk_base) {
+                                           typename Cfg::T* ring, uint64_t* full, uint64_t* empty, IterShared& sh,
+                                           int& chunk_base) {
     using T = typename Cfg::T;
     constexpr int CH = Cfg::CH, LDS = Cfg::LDS, TI = Cfg::TI, CONS = Cfg::CONS;
     constexpr bool kF32 = std::is_same<T, float>::value;
@@ -819,23 +820,49 @@ __device__ __noinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wave& 
                 }
             }
             }
-            // every warp is done with the stage (or a wait gave up: all leave together);
-            // each warp copies its rows of the chunk Cfg::STAGES further on into it
-            if (__syncthreads_or(!okw)) {
-                ok = false;
-                break;
-            }
-            if (k + Cfg::STAGES < total) {
-                issue_part<Cfg>(f, ring + size_t(s) * stage_elems<Cfg>(), &full[s], c_lo + k + Cfg::STAGES, nch, nrow, ncol,
-                              ctile, cvar);
-                issued = k + Cfg::STAGES + 1;
+            if constexpr (Cfg::STAGES >= 3) {
+                // Release without a CTA barrier: this warp arrives on the stage's empty
+                // barrier; after chunk k it copies its rows of chunk k + STAGES - 1 into the
+                // stage of chunk k - 1 once every warp has released that one.  Warps may
+                // drift apart by up to a chunk without blocking; the copy lands while the
+                // CTA computes chunk k + 1.
+                if (!okw) {
+                    ok = false;
+                    break;
+                }
+                __syncwarp();
+                if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+                const int kr = k - 1 + Cfg::STAGES;
+                if (k >= 1 && kr < total) {
+                    const int pr = pos - 1, sr = pr % Cfg::STAGES;
+                    if (!mbar_wait_or_abort(&empty[sr], (pr / Cfg::STAGES) & 1, gctl, tmo, &sh.abort)) {
+                        sh.abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    issue_part<Cfg>(f, ring + size_t(sr) * stage_elems<Cfg>(), &full[sr], c_lo + kr, nch, nrow, ncol,
+                                    ctile, cvar);
+                    issued = kr + 1;
+                }
+            } else {
+                // two stages: every warp is done with the stage (or a wait gave up: all leave
+                // together); each warp copies its rows of the chunk STAGES further on into it
+                if (__syncthreads_or(!okw)) {
+                    ok = false;
+                    break;
+                }
+                if (k + Cfg::STAGES < total) {
+                    issue_part<Cfg>(f, ring + size_t(s) * stage_elems<Cfg>(), &full[s], c_lo + k + Cfg::STAGES, nch,
+                                    nrow, ncol, ctile, cvar);
+                    issued = k + Cfg::STAGES + 1;
+                }
             }
         }
         if (__syncthreads_or(!ok)) {
             // A wait gave up (status recorded).  Give the copies still in flight a bounded
             // chance to land before the CTA leaves.
             if (tid == 0)
-                for (int k2 = k; k2 < issued; ++k2) {
+                for (int k2 = k; k2 < min(total, max(issued, k + Cfg::STAGES)); ++k2) {
                     const int pos = base + k2;
                     const unsigned long long t0 = global_ns();
                     while (!mbar_try_wait(&full[pos % Cfg::STAGES], (pos / Cfg::STAGES) & 1) &&
@@ -1128,13 +1155,17 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
     T* ring = reinterpret_cast<T*>(smem_raw);
     const size_t ring_or_sort = ring_bytes<Cfg>() > size_t(kSortMax) * 8 ? ring_bytes<Cfg>() : size_t(kSortMax) * 8;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + ring_or_sort);
+    uint64_t* empty = full + kStages;
     volatile Ctl* vc = ctl;
     // A failure recorded before this launch: every CTA reads it before the first
     // barrier, so all of them leave together.
     if (vc->status != 0) return;
     const unsigned long long tmo = vc->timeout_ns;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < Cfg::STAGES; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < Cfg::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], Cfg::CONS / 32);
+        }
         sh.abort = 0;
         fence_barrier_init();
     }
@@ -1146,7 +1177,7 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
     while (!vc->done) {
         const Wave wv = {vc->ntiles, vc->ncol, vc->nrow};
         const Span sp = single_span((long long)wv.ntiles * (f.ld / kSub), gridDim.x);
-        if (!compute_phase<Cfg>(f, ctl, wv, sp, ring, full, sh, chunk_base)) {
+        if (!compute_phase<Cfg>(f, ctl, wv, sp, ring, full, empty, sh, chunk_base)) {
             ctl->abort = 1;
             return;
         }
@@ -1286,11 +1317,15 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
     T* ring = reinterpret_cast<T*>(smem_raw);
     const size_t ring_or_sort = ring_bytes<Cfg>() > size_t(kSortMax) * 8 ? ring_bytes<Cfg>() : size_t(kSortMax) * 8;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + ring_or_sort);
+    uint64_t* empty = full + kStages;
     volatile Ctl* vb = bctl;
     if (vb->status != 0) return;
     const unsigned long long tmo = vb->timeout_ns;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < Cfg::STAGES; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < Cfg::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], Cfg::CONS / 32);
+        }
         sh.abort = 0;
         fence_barrier_init();
     }
@@ -1314,7 +1349,7 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
                 for (int d = last_le(bs.uoff, count, lo); d < count && bs.uoff[d] < hi; ++d) {
                     if (bs.uoff[d + 1] == bs.uoff[d]) continue;   // no units this wave
                     const Span sp{bs.uoff[d], utot, G, cta_of_unit(bs.uoff[d], utot, G)};
-                    if (!compute_phase<Cfg>(fits[d], bctl, bs.wave[d], sp, ring, full, sh, chunk_base)) {
+                    if (!compute_phase<Cfg>(fits[d], bctl, bs.wave[d], sp, ring, full, empty, sh, chunk_base)) {
                         bctl->abort = 1;
                         return;
                     }
