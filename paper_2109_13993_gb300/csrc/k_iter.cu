@@ -83,6 +83,11 @@ using CfgF32 = PairShape<float, 32, 32, 256, kChunk, kChunk + 4, 3, 2>;      // 
 using CfgF16 = PairShape<float, 64, 16, 256, kChunk, kChunk + 4, 2, 2>;      // FP32, 64 x 16 tiles
 using CfgD = PairShape<double, 32, 32, 256, kChunk64, kChunk64 + 2, 3, 1>;   // FP64 path
 
+// The kernels' dynamic shared memory (copy ring, sort area, mbarriers).  Referenced by
+// name in the compute loop so that its loads are shared-memory loads with 32-bit
+// addresses (a generic pointer argument would make them generic loads).
+extern __shared__ __align__(128) unsigned char smem_dyn[];
+
 constexpr int kSortMax = 8192;   // candidate sort in shared memory up to this many variables
 
 template <class Cfg>
@@ -731,7 +736,7 @@ __device__ __noinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wave& 
             const int s = pos % Cfg::STAGES;
             const bool okw = mbar_wait_or_abort(&full[s], (pos / Cfg::STAGES) & 1, gctl, tmo, &sh.abort);
             if (!okw) sh.abort = 1;
-            const T* st = ring + size_t(s) * stage_elems<Cfg>();
+            const T* st = reinterpret_cast<const T*>(smem_dyn) + size_t(s) * stage_elems<Cfg>();
             const T* R0 = st + rsl[0] * LDS;
             const T* R1 = st + rsl[1] * LDS;
             const T* C0 = st + (TI + csl[0]) * LDS;
@@ -1148,7 +1153,7 @@ __device__ __noinline__ void remove_cov_phase(const Fit& f, int vb, int vG) {
 // ------------------------------------------------------------------ the iteration kernel
 template <class Cfg>
 __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int it) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem_raw = smem_dyn;
     __shared__ IterShared sh;
     using T = typename Cfg::T;
     Ctl* ctl = f.ctl;
@@ -1309,7 +1314,7 @@ __device__ __forceinline__ int last_le(const I* off, int count, long long v) {
 template <class Cfg>
 __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __restrict__ fits, int count, int maxp,
                                                                Ctl* bctl) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem_raw = smem_dyn;
     __shared__ IterShared sh;
     __shared__ BatchShared bs;
     using T = typename Cfg::T;
