@@ -541,6 +541,32 @@ __device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
         if (tid == 0)
             for (int w = 0; w < NTH / 32; ++w) second = fmin(second, s_min[w]);
     }
+    if (nc == 0) {
+        // the iteration ends: its root, and the per-row coefficients 1/sqrt(1 - Sigma[w,root]^2)
+        // of UpdateData and UpdateCovMat, computed here once for all rows in parallel
+        __shared__ int s_root;
+        if (tid == 0) s_root = f.has_forced ? f.forced[it] : vc->best_var;
+        __syncthreads();
+        const int root = s_root;
+        const double* rootrow = f.sig + size_t(root) * p;
+        const bool f32 = f.precision == LINGAM_MIXED;
+        for (int k = tid; k < r; k += NTH) {
+            const int w = ld2(f.sigma + k);
+            f.prev[w] = ld2(f.part + w);
+            if (w == root) {
+                f.flags[w] = 0;
+                f.inv_root[w] = 0.0;
+                continue;
+            }
+            const double c = rootrow[w];
+            double om = fma(-c, c, 1.0);
+            if (!(om > degenerate_om(f32))) {
+                set_status(ctl, LINGAM_EDEGENERATE);
+                om = 1.0;
+            }
+            f.inv_root[w] = 1.0 / sqrt(om);
+        }
+    }
     if (tid == 0) {
         if (nc == 0) {
             const int root = f.has_forced ? f.forced[it] : vc->best_var;
@@ -1039,43 +1065,23 @@ __device__ __forceinline__ void merge_phase(const Fit& f, const Wave& wv, const 
 }
 
 // ------------------------------------------------------------------ removal phases
-// UpdateData (Algorithm 7) with the new H(x_w) terms; rows of U spread over the CTAs.
+// UpdateData (Algorithm 7) with the new H(x_w) terms; rows of U spread over the
+// (virtual) CTAs, all threads of a CTA on one row.  The row coefficients
+// 1/sqrt(1 - Sigma[w,root]^2) were computed by the iteration's last wave finalisation.
 template <class Cfg>
 __device__ __noinline__ void remove_data_phase(const Fit& f, IterShared& sh, int vb, int vG) {
     using T = typename Cfg::T;
     constexpr int NTH = Cfg::CONS;
-    Ctl* ctl = f.ctl;
-    volatile Ctl* vc = ctl;
+    volatile Ctl* vc = f.ctl;
     const int r = vc->r, root = vc->root, p = f.p, ld = f.ld, tid = threadIdx.x;
     const int lane = tid & 31, wid = tid >> 5;
+    const double* rootrow = f.sig + size_t(root) * p;
+    const T* xr = static_cast<const T*>(f.xt) + size_t(root) * ld;
     for (int k = vb; k < r; k += vG) {
         const int w = ld2(f.sigma + k);
-        if (tid == 0) f.prev[w] = ld2(f.part + w);
-        if (w == root) {
-            if (tid == 0) {
-                f.flags[w] = 0;
-                f.inv_root[w] = 0.0;
-            }
-            continue;
-        }
-        // coefficients of this row, computed once (FP64 is a slow pipe on this GPU)
-        if (tid == 0) {
-            const double c0 = f.sig[size_t(w) * p + root];
-            double om = fma(-c0, c0, 1.0);
-            if (!(om > degenerate_om(std::is_same<T, float>::value))) {
-                set_status(ctl, LINGAM_EDEGENERATE);
-                om = 1.0;
-            }
-            const double inv0 = 1.0 / sqrt(om);
-            f.inv_root[w] = inv0;
-            sh.dred[30] = c0;
-            sh.dred[31] = inv0;
-        }
-        __syncthreads();
-        const double c = sh.dred[30], inv = sh.dred[31];
-        __syncthreads();
+        if (w == root) continue;
+        const double c = rootrow[w], inv = ld2(f.inv_root + w);
         T* xw = static_cast<T*>(f.xt) + size_t(w) * ld;
-        const T* xr = static_cast<const T*>(f.xt) + size_t(root) * ld;
         T lcc = T(0), g = T(0);
         if constexpr (std::is_same<T, float>::value) {
             const float cc = float(c), ii = float(inv);
@@ -1104,7 +1110,6 @@ __device__ __noinline__ void remove_data_phase(const Fit& f, IterShared& sh, int
             }
         }
         // per-thread sums in the working precision, warp trees, then the warp sums in FP64
-        // by one thread
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             lcc += __shfl_xor_sync(0xffffffffu, lcc, o);
@@ -1128,9 +1133,11 @@ __device__ __noinline__ void remove_data_phase(const Fit& f, IterShared& sh, int
 }
 
 // UpdateCovMat (Algorithm 8 / Eq. CovUpdate) on the normalised rows, in FP64, for
-// w, j in U without the root; rows spread over the CTAs, columns in index order.
-// Sigma is symmetric, so Sigma[j,root] is read from the root's row (contiguous).
-// The root's row and column are only read, so the update is done in place.
+// w, j in U without the root; this CTA's rows (k = vb, vb + vG, ... of the candidate
+// list) against every partner j of the list.  Sigma is symmetric, so Sigma[j,root] is
+// the root's row; the root's row and column are only read, so the update is in place.
+// When the list fits, the partners' indices, Sigma[root, j] and 1/sqrt(1-Sigma[root,j]^2)
+// are staged in the (idle) copy ring first, so each element is one read-modify-write.
 template <class Cfg>
 __device__ __noinline__ void remove_cov_phase(const Fit& f, int vb, int vG) {
     constexpr int NTH = Cfg::CONS;
@@ -1138,15 +1145,44 @@ __device__ __noinline__ void remove_cov_phase(const Fit& f, int vb, int vG) {
     const int r = vc->r, root = vc->root, p = f.p, tid = threadIdx.x;
     const double* rootrow = f.sig + size_t(root) * p;
     const int nmine = r > vb ? (r - 1 - vb) / vG + 1 : 0;
-    const long long total = (long long)nmine * p;
+    if (nmine == 0) return;
+    const size_t stage_bytes = size_t(r) * (sizeof(int) + 2 * sizeof(double));
+    if (stage_bytes <= ring_bytes<Cfg>()) {
+        double* s_rj = reinterpret_cast<double*>(smem_dyn);
+        double* s_ij = s_rj + r;
+        int* s_j = reinterpret_cast<int*>(s_ij + r);
+        for (int jj = tid; jj < r; jj += NTH) {
+            const int j = ld2(f.sigma + jj);
+            s_j[jj] = j;
+            s_rj[jj] = rootrow[j];
+            s_ij[jj] = ld2(f.inv_root + j);
+        }
+        __syncthreads();
+        const long long total = (long long)nmine * r;
+#pragma unroll 4
+        for (long long idx = tid; idx < total; idx += NTH) {
+            const int m = int(idx / r), jj = int(idx - (long long)m * r);
+            const int kk = vb + m * vG;
+            const int w = s_j[kk];
+            const int j = s_j[jj];
+            if (w == root || j == root) continue;
+            double* row = f.sig + size_t(w) * p;
+            if (j == w) row[j] = 1.0;
+            else row[j] = (row[j] - s_rj[kk] * s_rj[jj]) * (s_ij[kk] * s_ij[jj]);
+        }
+        __syncthreads();
+        fence_proxy_async();   // the copy ring is written by bulk copies later
+    } else {
+        const long long total = (long long)nmine * p;
 #pragma unroll 2
-    for (long long idx = tid; idx < total; idx += NTH) {
-        const int m = int(idx / p), j = int(idx - (long long)m * p);
-        const int w = ld2(f.sigma + vb + m * vG);
-        if (w == root || j == root || !(ld2(f.flags + j) & kAlive)) continue;
-        double* row = f.sig + size_t(w) * p;
-        if (j == w) row[j] = 1.0;
-        else row[j] = (row[j] - rootrow[w] * rootrow[j]) * (ld2(f.inv_root + w) * ld2(f.inv_root + j));
+        for (long long idx = tid; idx < total; idx += NTH) {
+            const int m = int(idx / p), j = int(idx - (long long)m * p);
+            const int w = ld2(f.sigma + vb + m * vG);
+            if (w == root || j == root || !(ld2(f.flags + j) & kAlive)) continue;
+            double* row = f.sig + size_t(w) * p;
+            if (j == w) row[j] = 1.0;
+            else row[j] = (row[j] - rootrow[w] * rootrow[j]) * (ld2(f.inv_root + w) * ld2(f.inv_root + j));
+        }
     }
 }
 
@@ -1192,8 +1228,9 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
         if (!grid_sync(ctl, tmo)) return;
     }
     if (it < f.p - 1 && vc->root >= 0) {
+        // UpdateData and UpdateCovMat touch disjoint memory (the covariance's root column,
+        // from which the data coefficients come, is not written): no barrier between them
         remove_data_phase<Cfg>(f, sh, blockIdx.x, gridDim.x);
-        if (!grid_sync(ctl, tmo)) return;
         remove_cov_phase<Cfg>(f, blockIdx.x, gridDim.x);
     }
 }
@@ -1376,8 +1413,6 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
         for (int d = 0; d < count; ++d)
             if (bs.act[d])
                 remove_data_phase<Cfg>(fits[d], sh, int((blockIdx.x + 97ull * d) % gridDim.x), gridDim.x);
-        if (!grid_sync(bctl, tmo)) return;
-        batch_active(fits, count, it, 1, bs);
         for (int d = 0; d < count; ++d)
             if (bs.act[d]) remove_cov_phase<Cfg>(fits[d], int((blockIdx.x + 97ull * d) % gridDim.x), gridDim.x);
         if (!grid_sync(bctl, tmo)) return;
