@@ -281,7 +281,7 @@ def run_ours(args, rank: int, world: int):
     props = torch.cuda.get_device_properties(dev)
     bus = getattr(props, "pci_bus_id", None)
     bus_id = f"{bus:02x}:00" if isinstance(bus, int) else None
-    step_ms, pair_ms, pairs, launches = [], [], [], []
+    step_ms, pair_ms, pairs, launches, phases = [], [], [], [], []
     with ClockSampler(bus_id) as clk:
         for _ in range(args.steps):
             flush.zero_()
@@ -293,6 +293,7 @@ def run_ours(args, rank: int, world: int):
             torch.cuda.synchronize(dev)
             step_ms.append(e0.elapsed_time(e1))
             pair_ms.append(res.times_ms["pair"])
+            phases.append((res.times_ms["compute"], res.times_ms["merge"], res.times_ms["remove"]))
             pairs.append(res.pairs_total)
             launches.append(res.kernel_launches)
     clocks = clk.summary()
@@ -333,6 +334,12 @@ def run_ours(args, rank: int, world: int):
                 "traffic_basis": "ncu dram__bytes_read+write of one launch (iteration 2 of a fit, cold caches)",
                 "kernel": "k_iteration<float>",
                 "peak_basis": f"SFU: 4 ex2 + 1/16 lg2 per pair-sample, {nsm} SMs x 32 ex2/clk at sm_max {sm_max:.0f} MHz"}
+    # the same work over the pair-compute phases of the waves alone (device timer; the rest
+    # of each launch is merging, wave finalisation, removal and grid barriers)
+    ph = np.mean(np.array(phases), axis=0)
+    comp = float(np.sum(pairs)) * n / (float(np.sum([x[0] for x in phases])) / 1000.0)
+    roofline["compute_phase"] = {"achieved": comp / 1e9, "frac": comp / peak,
+                                 "ms_per_step": {"pair_compute": ph[0], "merge_finalize": ph[1], "removal": ph[2]}}
 
     line = {"metric": "pair-sample evals/s (unpruned-equivalent) at p=1000, n=1e4, mixed path",
             "value": value, "unit": "pair-samples/s", "n_gpus": world, "steps": args.steps,

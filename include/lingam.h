@@ -93,6 +93,11 @@ typedef struct {
     long long kernel_launches;   /* kernels this call launched */
     double* t_pair_iter_ms;      /* NULL or a HOST array [p]: with opts.timing = 1, device time of the
                                     pair comparison of iteration k (iterations with r >= 2) */
+    /* With opts.timing = 1 (single fits): device wall time (global timer, summed over all
+       iterations) of the pair-compute phases of the waves, of their merge and finalisation
+       phases, and of the removals (UpdateData, UpdateCovMat); each interval ends at a grid
+       barrier, so it covers the slowest CTA.  0 otherwise. */
+    double t_compute_ms, t_merge_ms, t_remove_ms;
 } lingam_report;
 
 /* Fills *opts with the defaults: MIXED, F32, prune = reuse = 1, autotuned

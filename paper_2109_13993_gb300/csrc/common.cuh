@@ -67,9 +67,9 @@ struct Ctl {
     int bar_gen;         // grid barrier: generation
     int abort;           // set when a CTA gives up a wait; the others then leave too
     int pad1;
+    unsigned long long phase_ns[3];   // with timing: pair compute, merge + finalise, removal (CTA 0)
 };
 
-// Device pointers of one fit, carved out of the caller's workspace.
 // Where a batch problem's samples come from: row i of the problem is the row of
 // x with stride ld (elements of the input type), sample t at column t, or at
 // column idx[t] for a bootstrap resample.
@@ -79,6 +79,7 @@ struct SrcDesc {
     long long ld;
 };
 
+// Device pointers of one fit, carved out of the caller's workspace.
 struct Fit {
     int p;               // variables
     int n;               // samples
@@ -88,6 +89,7 @@ struct Fit {
     int reuse;           // pair reuse on
     int has_forced;      // forced order given
     int want_scores;     // fill the per-iteration score matrix
+    int timing;          // accumulate the phase times in Ctl::phase_ns
     void* xt;            // p x ld normalised data (float or double)
     double* mu;          // [p] row means
     double* sd;          // [p] row standard deviations (divisor n-1)

@@ -1215,6 +1215,10 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
     if (blockIdx.x == 0) plan_phase<Cfg::CONS, Cfg::TI, Cfg::TJ>(f, it, smem_raw, sh.red);
     if (!grid_sync(ctl, tmo)) return;
     int chunk_base = 0;
+    // phase times (opts.timing): CTA 0's global timer at the phase boundaries, which follow
+    // grid barriers, so each interval covers the slowest CTA of the phase
+    const bool timed = f.timing && blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long tph = timed ? global_ns() : 0;
     while (!vc->done) {
         const Wave wv = {vc->ntiles, vc->ncol, vc->nrow};
         const Span sp = single_span((long long)wv.ntiles * (f.ld / kSub), gridDim.x);
@@ -1223,15 +1227,26 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
             return;
         }
         if (!grid_sync(ctl, tmo)) return;
+        if (timed) {
+            const unsigned long long t = global_ns();
+            ctl->phase_ns[0] += t - tph;
+            tph = t;
+        }
         merge_phase<Cfg>(f, wv, sp, it, sh, ring);
         fence_proxy_async();   // the merge used the copy ring as scratch
         if (!grid_sync(ctl, tmo)) return;
+        if (timed) {
+            const unsigned long long t = global_ns();
+            ctl->phase_ns[1] += t - tph;
+            tph = t;
+        }
     }
     if (it < f.p - 1 && vc->root >= 0) {
         // UpdateData and UpdateCovMat touch disjoint memory (the covariance's root column,
         // from which the data coefficients come, is not written): no barrier between them
         remove_data_phase<Cfg>(f, sh, blockIdx.x, gridDim.x);
         remove_cov_phase<Cfg>(f, blockIdx.x, gridDim.x);
+        if (timed) ctl->phase_ns[2] += global_ns() - tph;
     }
 }
 

@@ -204,6 +204,7 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
     Fit f = make_fit(base, L, p, n, o, rep && rep->scores);
     f.has_forced = o.forced_order != nullptr;
     f.forced = o.forced_order ? reinterpret_cast<const int*>(base + L.off_forced) : nullptr;
+    f.timing = o.timing ? 1 : 0;
 
 #define CK(call)                                  \
     do {                                          \
@@ -325,6 +326,9 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
                 }
             rep->t_pair_ms = tp;
             rep->kernel_launches = launches;
+            rep->t_compute_ms = o.timing ? double(ch.phase_ns[0]) * 1e-6 : 0.0;
+            rep->t_merge_ms = o.timing ? double(ch.phase_ns[1]) * 1e-6 : 0.0;
+            rep->t_remove_ms = o.timing ? double(ch.phase_ns[2]) * 1e-6 : 0.0;
         }
         if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) status = LINGAM_ECUDA;
         if (rep && status == LINGAM_OK) {
@@ -655,6 +659,7 @@ static int fit_many(std::vector<BatchItem>& items, void* workspace, const lingam
                 if (r->pairs_evaluated) cudaMemcpy(r->pairs_evaluated, f.rep_pairs, pk * 8, cudaMemcpyDefault);
                 if (r->scores) cudaMemcpy(r->scores, f.rep_scores, pk * pk * 8, cudaMemcpyDefault);
                 r->t_standardize_ms = r->t_gram_ms = r->t_order_ms = r->t_B_ms = r->t_pair_ms = -1.0;
+                r->t_compute_ms = r->t_merge_ms = r->t_remove_ms = -1.0;
             }
         }
         po += pk;

@@ -37,7 +37,8 @@ class Report(ctypes.Structure):
                 ("scores", _c_dbl_p), ("t_standardize_ms", ctypes.c_double), ("t_gram_ms", ctypes.c_double),
                 ("t_order_ms", ctypes.c_double), ("t_B_ms", ctypes.c_double), ("pairs_total", ctypes.c_longlong),
                 ("pairs_unpruned", ctypes.c_longlong), ("t_pair_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_longlong), ("t_pair_iter_ms", _c_dbl_p)]
+                ("kernel_launches", ctypes.c_longlong), ("t_pair_iter_ms", _c_dbl_p),
+                ("t_compute_ms", ctypes.c_double), ("t_merge_ms", ctypes.c_double), ("t_remove_ms", ctypes.c_double)]
 
 
 class LingamError(RuntimeError):
@@ -232,7 +233,8 @@ def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, for
         raise LingamError(st, status_string(st))
     return FitResult(order=order, B=B, root_score=rs, margin_lb=mg, pairs_evaluated=pe, scores=sc,
                      times_ms={"standardize": rep.t_standardize_ms, "gram": rep.t_gram_ms,
-                               "order": rep.t_order_ms, "B": rep.t_B_ms, "pair": rep.t_pair_ms},
+                               "order": rep.t_order_ms, "B": rep.t_B_ms, "pair": rep.t_pair_ms,
+                               "compute": rep.t_compute_ms, "merge": rep.t_merge_ms, "remove": rep.t_remove_ms},
                      pairs_total=int(rep.pairs_total), pairs_unpruned=int(rep.pairs_unpruned),
                      kernel_launches=int(rep.kernel_launches), t_pair_iter_ms=tpi)
 
