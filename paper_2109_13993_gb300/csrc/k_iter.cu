@@ -414,16 +414,23 @@ __device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
     // 2. column contributions max(0, I(row, col))^2 = min(0, I(col, row))^2 in tile order
     //    (staged in shared memory by all threads, then summed per column);
     // 3. threshold = lowest complete score (lowest variable index on ties)
+    // (column parts of every item of every tile: (tile, part) in order)
+    constexpr int PARTS = NTH / 64;
+    const int nparts = ntiles * PARTS;
+    // all loads at once: thread (slice sl, column c) sums parts sl, sl + SL, ... of column c,
+    // then the SL slice sums of a column are added in slice order (a fixed order)
+    constexpr int SL = NTH / TJ;
+    static_assert(SL <= 32, "slices fit the staging array");
     __shared__ double s_col[32 * 33];
     double tot = 0.0;
-    for (int t0 = 0; t0 < ntiles; t0 += 32) {
-        for (int k = tid; k < 32 * TJ; k += NTH) {
-            const int t = t0 + k / TJ;
-            s_col[(k / TJ) * 33 + (k % TJ)] = t < ntiles ? ld2(f.colsum + t * TJ + (k % TJ)) : 0.0;
-        }
+    {
+        const int c = tid % TJ, sl = tid / TJ;
+        double ps = 0.0;
+        for (int tp = sl; tp < nparts; tp += SL) ps += ld2(f.colsum + size_t(tp) * TJ + c);
+        s_col[sl * 33 + c] = ps;
         __syncthreads();
         if (tid < TJ)
-            for (int j = 0; j < 32 && t0 + j < ntiles; ++j) tot += s_col[j * 33 + tid];
+            for (int j = 0; j < SL; ++j) tot += s_col[j * 33 + tid];
         __syncthreads();
     }
     if (tid < 32) {
@@ -965,7 +972,9 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
 #pragma unroll
         for (int k = 0; k < 32; ++k) scratch[wid * 1056 + lane * 33 + k] = acc[k];
         __syncthreads();
-        // 2. one thread per pair: warps' sums in warp order, then I
+        // 2. one thread per pair: warps' sums in warp order, then I (staged past the warp sums,
+        //    which other threads may still be reading)
+        T* sI = scratch + NW * 1056;
         if (tid < 256) {
             T tot[4] = {T(0), T(0), T(0), T(0)};
             for (int w = 0; w < NW; ++w)
@@ -996,61 +1005,57 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
                 }
                 if (!isfinite(double(I))) set_status(ctl, LINGAM_EDEGENERATE);
             }
-            ibuf[(size_t(t) * TI + e_loc) * TJ + cc] = I;
+            // stage the item's I: its rows are complete (all TJ columns), local row index
+            // = row within the item's first half, then the second half (TI / 2 further down)
+            const int el = ct / (TJ / 2) - part * (64 / (TJ / 2)) + (q >> 1) * (64 / (TJ / 2));
+            sI[el * (TJ + 1) + cc] = I;
+        }
+        __syncthreads();
+        // 3. this item's rows' contributions min(0, I)^2 over all columns (complete rows of
+        //    the tile), and its part of each column's contributions max(0, I)^2; the wave's
+        //    last item sums the column parts of all tiles and items in a fixed order
+        constexpr int IR = 2 * (64 / (TJ / 2));   // rows of an item
+        static_assert(size_t(NW) * 1056 + IR * (TJ + 1) <= ring_bytes<Cfg>() / sizeof(T),
+                      "the merge scratch must fit in the copy ring");
+        if (tid < IR) {
+            const int e_loc = (tid < IR / 2 ? part * (IR / 2) + tid : part * (IR / 2) + tid - IR / 2 + TI / 2);
+            const int e = t * TI + e_loc;
+            double rs;
+            if constexpr (kF32) {
+                FF acc;
+                for (int cc = 0; cc < TJ; ++cc) acc.add_sq(fminf(sI[tid * (TJ + 1) + cc], 0.f));
+                rs = acc.value();
+            } else {
+                rs = 0.0;
+                for (int cc = 0; cc < TJ; ++cc) {
+                    const double m = fmin(double(sI[tid * (TJ + 1) + cc]), 0.0);
+                    rs = fma(m, m, rs);
+                }
+            }
+            if (e < nrow) f.rowsum[e] = rs;
+        } else if (tid >= 32 && tid < 32 + TJ) {
+            const int cc = tid - 32;
+            double cs;
+            if constexpr (kF32) {
+                FF acc;
+                for (int el = 0; el < IR; ++el) acc.add_sq(fmaxf(sI[el * (TJ + 1) + cc], 0.f));
+                cs = acc.value();
+            } else {
+                cs = 0.0;
+                for (int el = 0; el < IR; ++el) {
+                    const double m = fmax(double(sI[el * (TJ + 1) + cc]), 0.0);
+                    cs = fma(m, m, cs);
+                }
+            }
+            f.colsum[(size_t(t) * PARTS + part) * TJ + cc] = cs;
         }
         __threadfence();
         __syncthreads();
-        if (tid == 0) sh.flag = (atomicAdd(f.tile_cnt + t, 1) == PARTS - 1);
+        if (tid == 0) sh.flag = (atomicAdd(&ctl->merged, 1) == ntiles * PARTS - 1);
         __syncthreads();
         if (sh.flag) {
-            // 3. the tile's last item: per-row and per-column contributions in FP64, from the
-            //    tile's I staged in shared memory (row stride TJ + 1)
             __threadfence();
-            const T* It = ibuf + size_t(t) * TI * TJ;
-            for (int k = tid; k < TI * TJ; k += CONS) scratch[(k / TJ) * (TJ + 1) + (k % TJ)] = __ldcg(It + k);
-            __syncthreads();
-            if constexpr (kF32) {
-                // squares summed exactly enough (float-float) that a variable's score does not
-                // depend on how its pairs were grouped into tiles and waves
-                if (tid < TI) {
-                    const int e = t * TI + tid;
-                    FF acc;
-                    for (int cc = 0; cc < TJ; ++cc) acc.add_sq(fminf(scratch[tid * (TJ + 1) + cc], 0.f));
-                    if (e < nrow) f.rowsum[e] = acc.value();
-                } else if (tid < TI + TJ) {
-                    const int cc = tid - TI;
-                    FF acc;
-                    for (int e = 0; e < TI; ++e) acc.add_sq(fmaxf(scratch[e * (TJ + 1) + cc], 0.f));
-                    f.colsum[t * TJ + cc] = acc.value();
-                }
-            } else {
-                if (tid < TI) {
-                    const int e = t * TI + tid;
-                    double s = 0.0;
-                    for (int cc = 0; cc < TJ; ++cc) {
-                        const double m = fmin(double(scratch[tid * (TJ + 1) + cc]), 0.0);
-                        s = fma(m, m, s);
-                    }
-                    if (e < nrow) f.rowsum[e] = s;
-                } else if (tid < TI + TJ) {
-                    const int cc = tid - TI;
-                    double s = 0.0;
-                    for (int e = 0; e < TI; ++e) {
-                        const double m = fmax(double(scratch[e * (TJ + 1) + cc]), 0.0);
-                        s = fma(m, m, s);
-                    }
-                    f.colsum[t * TJ + cc] = s;
-                }
-            }
-            if (tid == 0) f.tile_cnt[t] = 0;
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) sh.flag = (atomicAdd(&ctl->merged, 1) == ntiles - 1);
-            __syncthreads();
-            if (sh.flag) {
-                __threadfence();
-                wave_finalize<CONS, TI, TJ>(f, it, sh.red);
-            }
+            wave_finalize<CONS, TI, TJ>(f, it, sh.red);
         }
         __syncthreads();
     }

@@ -84,7 +84,7 @@ static Layout make_layout(long long p, long long n, int precision, int input_dty
     L.off_forced = take(P * 4);
     L.off_scratch = take(P * 4);
     L.off_rowsum = take(P * 8);
-    L.off_colsum = take(size_t(L.maxtiles) * kTJ * 8);
+    L.off_colsum = take(size_t(L.maxtiles) * (kPairThreads / 64) * kTJ * 8);   // per (tile, merge item)
     // one partial-moment slot per (tile, CTA) segment; slot index tile + CTA, and a wave never
     // uses more CTAs than it has (tile, 32-sample group) units
     const size_t units = size_t(L.maxtiles) * size_t(L.ld / kSub);
