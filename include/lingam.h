@@ -23,13 +23,18 @@
  *   - Errors are returned as lingam_status codes; nothing is thrown across
  *     the ABI.  Outputs are written only when the call returns LINGAM_OK.
  *   - The caller owns every buffer, the workspace included.  The library
- *     allocates no memory.  The only state kept between calls is the
- *     pair-tile autotuner's table (lingam_autotune) and the address of the
- *     static scratch area (lingam_fit_static).
+ *     allocates no device memory for data.  State kept between calls: the
+ *     pair-tile autotuner's table (lingam_autotune), the address of the
+ *     static scratch area (lingam_fit_static), the executable graphs of batch
+ *     calls (lingam_fit_batch, lingam_fit_bootstrap; keyed by workspace and
+ *     shapes) and, per host thread and device, eight streams and their events
+ *     for the independent per-problem launches of a batch.
  *   - Data pointers may point to host or device memory; the library tells
  *     them apart with cudaPointerGetAttributes.  Host buffers are copied
- *     inside the call.  All device work runs on opts->stream and the call
- *     returns after that stream has drained (it is synchronous).
+ *     inside the call.  All device work is ordered on opts->stream (a batch
+ *     forks its per-problem covariances onto the library's streams and joins
+ *     them back into it) and the call returns after that stream has drained
+ *     (it is synchronous).
  *   - The device is the CUDA device current on the calling thread.
  */
 #ifndef LINGAM_H

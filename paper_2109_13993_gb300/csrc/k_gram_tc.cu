@@ -327,8 +327,17 @@ __global__ void k_gram_tc_reduce(Fit f, const float2* __restrict__ partial, cons
         const int r = e / kGM, c = e % kGM;
         const int i = bi * kGM + r, j = bj * kGM + c;
         if (i >= p || j >= p || i > j) continue;
+        // split order; eight loads in flight at a time
         double s = 0.0;
-        for (int sp = 0; sp < nsplit; ++sp) {
+        int sp = 0;
+        for (; sp + 8 <= nsplit; sp += 8) {
+            float2 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = partial[((size_t(sp + q) * ntri + tile) * kGM + r) * kGM + c];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) s += double(v[q].x) + double(v[q].y);
+        }
+        for (; sp < nsplit; ++sp) {
             const float2 v = partial[((size_t(sp) * ntri + tile) * kGM + r) * kGM + c];
             s += double(v.x) + double(v.y);
         }

@@ -78,7 +78,7 @@ static Layout make_layout(long long p, long long n, int precision, int input_dty
     L.off_prev = take(P * 8);
     L.off_flags = take(P * 4);
     L.off_sigma = take(P * 4);
-    L.off_rows = take(P * 4);
+    L.off_rows = take((P + kTJ) * 4);   // the finalisation may write up to kTJ past the rows
     L.off_cols = take(kTJ * 4);
     L.off_order = take(P * 4);
     L.off_forced = take(P * 4);
@@ -435,6 +435,41 @@ static std::map<GraphKey, cudaGraphExec_t> g_graphs;
 
 static std::map<GraphKey, int> g_graph_seen;   // keys run once eagerly, captured on the next call
 
+// Streams for the independent per-problem launches of a batch (the covariances): forked
+// from the caller's stream by an event and joined back into it, so that they run
+// concurrently in eager calls and become parallel branches of a captured graph.  One set
+// per host thread and device, created on first use.
+struct ForkStreams {
+    static constexpr int kN = 8;
+    cudaStream_t s[kN] = {};
+    cudaEvent_t fork = nullptr, join[kN] = {};
+    bool ok = false;
+    void create() {
+        ok = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < kN && ok; ++i)
+            ok = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    }
+    ~ForkStreams() {
+        for (int i = 0; i < kN; ++i) {
+            if (s[i]) cudaStreamDestroy(s[i]);
+            if (join[i]) cudaEventDestroy(join[i]);
+        }
+        if (fork) cudaEventDestroy(fork);
+        cudaGetLastError();
+    }
+};
+static ForkStreams* fork_streams(int dev) {
+    thread_local std::map<int, ForkStreams> sets;
+    auto found = sets.find(dev);
+    if (found == sets.end()) {
+        found = sets.emplace(std::piecewise_construct, std::forward_as_tuple(dev), std::forward_as_tuple()).first;
+        found->second.create();
+    }
+    return found->second.ok ? &found->second : nullptr;
+}
+
 // The device work of a batch, enqueued on st.
 static cudaError_t enqueue_batch(char* ws, const BatchLayout& BL, const std::vector<Fit>& fits,
                                  const std::vector<Layout>& Ls, const lingam_opts& o, int rows, bool with_B,
@@ -445,12 +480,29 @@ static cudaError_t enqueue_batch(char* ws, const BatchLayout& BL, const std::vec
                                              reinterpret_cast<const int*>(ws + BL.off_rowoff), count, rows,
                                              o.precision, o.input_dtype, st);
     if (e != cudaSuccess) return e;
-    for (int k = 0; k < count; ++k) {
-        e = o.precision == LINGAM_MIXED
-                ? launch_gram_tc(fits[size_t(k)], ws + BL.region[size_t(k)] + Ls[size_t(k)].off_xin, fits[size_t(k)].partials, st)
-                : launch_gram(fits[size_t(k)], st);
-        if (e != cudaSuccess) return e;
+    // the problems' covariances, spread over the fork streams (every stream is joined back
+    // before any error returns, so a capture in progress stays well formed)
+    int dev = 0;
+    ForkStreams* fs = (count > 1 && cudaGetDevice(&dev) == cudaSuccess) ? fork_streams(dev) : nullptr;
+    int nfork = 0;
+    if (fs && cudaEventRecord(fs->fork, st) == cudaSuccess) {
+        for (; nfork < ForkStreams::kN && nfork < count; ++nfork)
+            if (cudaStreamWaitEvent(fs->s[nfork], fs->fork, 0) != cudaSuccess) break;
     }
+    cudaGetLastError();
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        cudaStream_t sk = nfork > 0 ? fs->s[k % nfork] : st;
+        e = o.precision == LINGAM_MIXED
+                ? launch_gram_tc(fits[size_t(k)], ws + BL.region[size_t(k)] + Ls[size_t(k)].off_xin, fits[size_t(k)].partials, sk)
+                : launch_gram(fits[size_t(k)], sk);
+    }
+    for (int i = 0; i < nfork; ++i) {
+        const cudaError_t ej = cudaEventRecord(fs->join[i], fs->s[i]) == cudaSuccess
+                                   ? cudaStreamWaitEvent(st, fs->join[i], 0)
+                                   : cudaErrorUnknown;
+        if (e == cudaSuccess) e = ej;
+    }
+    if (e != cudaSuccess) return e;
     Ctl* bctl = reinterpret_cast<Ctl*>(ws + BL.off_bctl);
     for (int c0 = 0; c0 < count; c0 += kBatchLaunchMax) {
         const int cnt = std::min(kBatchLaunchMax, count - c0);
