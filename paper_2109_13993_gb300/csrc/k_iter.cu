@@ -392,55 +392,101 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
 }
 
 // ------------------------------------------------------------------ wave finalisation
+// The wave a phase works on: its tiles, columns and rows.
+struct Wave {
+    int ntiles, ncol, nrow;
+};
+
 // Run by one CTA (the one that merged the wave's last tile).
 template <int NTH, int TI, int TJ>
-__device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
+__device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it, int* red) {
     Ctl* ctl = f.ctl;
     volatile Ctl* vc = ctl;
     const int tid = threadIdx.x;
-    const int ncol = vc->ncol, nrow = vc->nrow, ntiles = vc->ntiles;
+    const int ncol = wv.ncol, nrow = wv.nrow, ntiles = wv.ntiles;
     const int p = f.p, r = vc->r;
+    constexpr int PARTS = NTH / 64;
+    constexpr int SL = NTH / TJ;   // slices of the column parts
+    static_assert(SL <= 32, "slices fit the staging array");
+    static_assert(TJ <= 32 && NTH >= 64, "the wave's columns are threads 0 .. TJ - 1");
+    constexpr int kPre = 8;        // candidate positions per thread fetched ahead (r <= kPre * NTH)
+    __shared__ double s_col[32 * 33];
+    __shared__ double s_best;
+    __shared__ int s_bestv;
 
-    // 1. row contributions: min(0, I(row, col))^2 summed over the wave's columns
+    // Every load that depends on nothing written in this finalisation is issued first:
+    // the candidates in order, this thread's slice of the column parts, the columns, the
+    // running threshold and pair count.
+    int pv[kPre];
+#pragma unroll
+    for (int j = 0; j < kPre; ++j) {
+        const int k = j * NTH + tid;
+        pv[j] = k < r ? ld2(f.sigma + k) : -1;
+    }
+    // thread (slice sl, column c) sums parts sl, sl + SL, ... of column c in that order
+    const int nparts = ntiles * PARTS;
+    double ps = 0.0;
+    {
+        const int c = tid % TJ, sl = tid / TJ;
+        constexpr int kB = 8;
+        int tp = sl;
+        for (; tp + (kB - 1) * SL < nparts; tp += kB * SL) {
+            double v[kB];
+#pragma unroll
+            for (int q = 0; q < kB; ++q) v[q] = ld2(f.colsum + size_t(tp + q * SL) * TJ + c);
+#pragma unroll
+            for (int q = 0; q < kB; ++q) ps += v[q];
+        }
+        for (; tp < nparts; tp += SL) ps += ld2(f.colsum + size_t(tp) * TJ + c);
+    }
+    int cv = 0x7fffffff, cfl = 0;
+    double cpart = 0.0;
+    if (tid < ncol) {
+        cv = ld2(f.cols + tid);
+        cpart = ld2(f.part + cv);
+        cfl = ld2(f.flags + cv);
+    }
+    double best0 = INFINITY;
+    int bv0 = -1;
+    long long pairs0 = 0;
+    if (tid == 0) {
+        best0 = vc->best;
+        bv0 = vc->best_var;
+        pairs0 = vc->pairs_it;
+    }
+
+    // 1. row contributions min(0, I(row, col))^2 summed over the wave's columns.  The
+    //    columns are rows 0 .. ncol - 1 (thread e holds row e < ncol): their sums join
+    //    the column totals in step 3, in the same order of additions.
+    double col_rs = 0.0;
     if (f.reuse) {
 #pragma unroll 4
         for (int e = tid; e < nrow; e += NTH) {
             const int v = ld2(f.rows + e);
             const double add = ld2(f.rowsum + e);
-            f.part[v] = ld2(f.part + v) + add;
+            if (e < ncol)
+                col_rs = add;
+            else
+                f.part[v] = ld2(f.part + v) + add;
         }
     }
+    // 2. column contributions max(0, I(row, col))^2 = min(0, I(col, row))^2: the slice
+    //    sums of a column added in slice order (a fixed order)
+    s_col[(tid / TJ) * 33 + tid % TJ] = ps;
     __syncthreads();
-    // 2. column contributions max(0, I(row, col))^2 = min(0, I(col, row))^2 in tile order
-    //    (staged in shared memory by all threads, then summed per column);
-    // 3. threshold = lowest complete score (lowest variable index on ties)
-    // (column parts of every item of every tile: (tile, part) in order)
-    constexpr int PARTS = NTH / 64;
-    const int nparts = ntiles * PARTS;
-    // all loads at once: thread (slice sl, column c) sums parts sl, sl + SL, ... of column c,
-    // then the SL slice sums of a column are added in slice order (a fixed order)
-    constexpr int SL = NTH / TJ;
-    static_assert(SL <= 32, "slices fit the staging array");
-    __shared__ double s_col[32 * 33];
     double tot = 0.0;
-    {
-        const int c = tid % TJ, sl = tid / TJ;
-        double ps = 0.0;
-        for (int tp = sl; tp < nparts; tp += SL) ps += ld2(f.colsum + size_t(tp) * TJ + c);
-        s_col[sl * 33 + c] = ps;
-        __syncthreads();
-        if (tid < TJ)
-            for (int j = 0; j < SL; ++j) tot += s_col[j * 33 + tid];
-        __syncthreads();
-    }
+    if (tid < TJ)
+        for (int j = 0; j < SL; ++j) tot += s_col[j * 33 + tid];
+    // 3. the columns' complete scores; threshold = lowest complete score (lowest variable
+    //    index on ties)
     if (tid < 32) {
         double sc = INFINITY;
         int v = 0x7fffffff;
         if (tid < ncol) {
-            v = ld2(f.cols + tid);
-            sc = ld2(f.part + v) + tot;
+            v = cv;
+            sc = (f.reuse ? cpart + col_rs : cpart) + tot;
             f.part[v] = sc;
-            f.flags[v] = ld2(f.flags + v) | kColumned;
+            f.flags[v] = cfl | kColumned;
             if (f.want_scores) f.rep_scores[(size_t)it * p + v] = sc;
         }
 #pragma unroll
@@ -453,33 +499,31 @@ __device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
             }
         }
         if (tid == 0) {
-            const double best = vc->best;
-            const int bv = vc->best_var;
-            if (bv < 0 || sc < best || (sc == best && v < bv)) {
+            if (bv0 < 0 || sc < best0 || (sc == best0 && v < bv0)) {
+                best0 = sc;
+                bv0 = v;
                 ctl->best = sc;
                 ctl->best_var = v;
             }
-            ctl->pairs_it += f.reuse ? (long long)ncol * (ncol - 1) / 2 + (long long)ncol * (nrow - ncol)
-                                     : (long long)ncol * (nrow - 1);
+            pairs0 += f.reuse ? (long long)ncol * (ncol - 1) / 2 + (long long)ncol * (nrow - ncol)
+                              : (long long)ncol * (nrow - 1);
+            ctl->pairs_it = pairs0;
+            s_best = best0;
+            s_bestv = bv0;
         }
     }
     __syncthreads();
-    const double best = vc->best;
+    const double best = s_best;
+    const int bv = s_bestv;
 
     // 4. one pass over the candidates: prune (partial score above the threshold), pick
     //    the next columns (the first TJ live un-columned variables in candidate order)
     //    and list the next rows (every other row-eligible variable: un-columned ones with
-    //    reuse, all remaining ones without), both in candidate order.
-    // The candidates' flags and scores are fetched for all of this thread's positions
-    // first (independent loads), then the blocks are scanned in order.
-    constexpr int kPre = 8;   // positions per thread fetched ahead (r <= kPre * NTH)
-    int pv[kPre], pfl[kPre];
+    //    reuse, all remaining ones without), both in candidate order.  The rows are
+    //    written where they belong when the next wave has TJ columns (rows TJ, TJ + 1,
+    //    ...) and also to scratch, from which a wave of fewer columns copies them.
+    int pfl[kPre];
     double ppart[kPre];
-#pragma unroll
-    for (int j = 0; j < kPre; ++j) {
-        const int k = j * NTH + tid;
-        pv[j] = k < r ? ld2(f.sigma + k) : -1;
-    }
 #pragma unroll
     for (int j = 0; j < kPre; ++j) {
         pfl[j] = pv[j] >= 0 ? ld2(f.flags + pv[j]) : 0;
@@ -518,28 +562,39 @@ __device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
         // every pick is eligible; the row rank of an eligible non-pick is the rows listed
         // so far plus the eligible variables before it in this block minus the picks among them
         const int picked_before = min(nlive + pl, TJ) - min(nlive, TJ);
-        if (pick) f.cols[lrank] = v;
-        if (elig && !pick) f.scratch[nr + pe - picked_before] = v;
+        if (pick) {
+            f.cols[lrank] = v;
+            f.rows[lrank] = v;
+        }
+        if (elig && !pick) {
+            const int ri = nr + pe - picked_before;
+            f.scratch[ri] = v;
+            f.rows[TJ + ri] = v;
+        }
         const int picks_here = min(nlive + tl, TJ) - min(nlive, TJ);
         nlive += tl;
         nr += te - picks_here;
         __syncthreads();
     }
     const int nc = nlive < TJ ? nlive : TJ;
-    __syncthreads();
-    for (int k = tid; k < nc + nr; k += NTH) f.rows[k] = k < nc ? ld2(f.cols + k) : ld2(f.scratch + k - nc);
-    __syncthreads();
+    if (nc < TJ) {
+        for (int k = tid; k < nr; k += NTH) f.rows[nc + k] = ld2(f.scratch + k);
+        __syncthreads();
+    }
 
     // 6. no live variable left: the root is the complete variable of lowest score (or
     //    the forced one); the margin bound is the lowest other score (full if complete,
-    //    else a lower bound) minus the root's.
+    //    else a lower bound) minus the root's.  The candidates' scores are the ones
+    //    fetched for step 4 (step 4 changes flags only).
     double second = INFINITY;
     if (nc == 0) {
         __shared__ double s_min[32];
-        const int bv = vc->best_var;
-        for (int k = tid; k < r; k += NTH) {
-            const int v = ld2(f.sigma + k);
-            if (v != bv) second = fmin(second, ld2(f.part + v));
+        for (int base = 0, j = 0; base < r; base += NTH, ++j) {
+            const int k = base + tid;
+            if (k >= r) break;
+            const int v = j < kPre ? pv[j] : ld2(f.sigma + k);
+            const double pt = j < kPre ? ppart[j] : ld2(f.part + v);
+            if (v != bv) second = fmin(second, pt);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) second = fmin(second, __shfl_xor_sync(0xffffffffu, second, o));
@@ -548,18 +603,18 @@ __device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
         if (tid == 0)
             for (int w = 0; w < NTH / 32; ++w) second = fmin(second, s_min[w]);
     }
+    int root = -1;
     if (nc == 0) {
         // the iteration ends: its root, and the per-row coefficients 1/sqrt(1 - Sigma[w,root]^2)
         // of UpdateData and UpdateCovMat, computed here once for all rows in parallel
-        __shared__ int s_root;
-        if (tid == 0) s_root = f.has_forced ? f.forced[it] : vc->best_var;
-        __syncthreads();
-        const int root = s_root;
+        root = f.has_forced ? f.forced[it] : bv;
         const double* rootrow = f.sig + size_t(root) * p;
         const bool f32 = f.precision == LINGAM_MIXED;
-        for (int k = tid; k < r; k += NTH) {
-            const int w = ld2(f.sigma + k);
-            f.prev[w] = ld2(f.part + w);
+        for (int base = 0, j = 0; base < r; base += NTH, ++j) {
+            const int k = base + tid;
+            if (k >= r) break;
+            const int w = j < kPre ? pv[j] : ld2(f.sigma + k);
+            f.prev[w] = j < kPre ? ppart[j] : ld2(f.part + w);
             if (w == root) {
                 f.flags[w] = 0;
                 f.inv_root[w] = 0.0;
@@ -576,13 +631,12 @@ __device__ __noinline__ void wave_finalize(const Fit& f, int it, int* red) {
     }
     if (tid == 0) {
         if (nc == 0) {
-            const int root = f.has_forced ? f.forced[it] : vc->best_var;
             ctl->root = root;
             ctl->done = 1;
             f.order[it] = root;
-            f.rep_root_score[it] = ld2(f.part + root);
-            f.rep_margin[it] = second - vc->best;
-            f.rep_pairs[it] = vc->pairs_it;
+            f.rep_root_score[it] = root == bv ? best : ld2(f.part + root);
+            f.rep_margin[it] = second - best;
+            f.rep_pairs[it] = pairs0;
         } else {
             ctl->ncol = nc;
             ctl->nrow = nc + nr;
@@ -664,9 +718,6 @@ __device__ __forceinline__ void issue_part(const Fit& f, typename Cfg::T* stage,
 
 // ------------------------------------------------------------------ compute phase
 // Returns false when a wait gave up (the CTA then leaves the kernel).
-struct Wave {
-    int ntiles, ncol, nrow;
-};
 
 // Where one problem's (tile, 32-sample group) units sit in the wave's stream-K
 // partition: the units of all problems of the wave are concatenated, this problem's
@@ -948,7 +999,6 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
     const long long ng = ld / kSub;   // 32-sample groups per tile: the stream-K unit
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const T* parts = static_cast<const T*>(f.partials);
-    T* ibuf = static_cast<T*>(f.ibuf);
     const double n = double(f.n);
     const double pad_fix = double(ld - f.n) * kBeta;   // each zero padding sample added -beta
     {
@@ -956,6 +1006,13 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
         // slot offsets of the CTAs that hold partial moments of tile t
         const int b_first = cta_of_unit(sp.off + (long long)t * ng, sp.utot, sp.G) - sp.b_base;
         const int b_last = cta_of_unit(sp.off + (long long)(t + 1) * ng - 1, sp.utot, sp.G) - sp.b_base;
+        // thread tid < 256 evaluates pair tid of the item = pair (tid & 3) of compute thread
+        // part * 64 + tid / 4; its variables are fetched together with the partial moments
+        const int ct = part * 64 + (tid >> 2), q = tid & 3;
+        const int e_loc = ct / (TJ / 2) + (q >> 1) * (TI / 2), cc = ct % (TJ / 2) + (q & 1) * (TJ / 2);
+        const int e = t * TI + e_loc;
+        const int vi = (tid < 256 && e < nrow) ? ld2(f.rows + e) : -1;
+        const int vj = (tid < 256 && cc < ncol) ? ld2(f.cols + cc) : -1;
         // 1. per warp: slots b_first + wid, + NW, ...; each lane 32 of the item's 1024 values
         T acc[32];
 #pragma unroll
@@ -983,12 +1040,6 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
                     const int v = tid * 4 + k;   // value index in the item
                     tot[k] += scratch[w * 1056 + (v >> 5) * 33 + (v & 31)];
                 }
-            // pair tid of the item = pair (tid & 3) of compute thread part * 64 + tid / 4
-            const int ct = part * 64 + (tid >> 2), q = tid & 3;
-            const int e_loc = ct / (TJ / 2) + (q >> 1) * (TI / 2), cc = ct % (TJ / 2) + (q & 1) * (TJ / 2);
-            const int e = t * TI + e_loc;
-            const int vi = e < nrow ? ld2(f.rows + e) : -1;
-            const int vj = cc < ncol ? ld2(f.cols + cc) : -1;
             bool okp = vi >= 0 && vj >= 0;
             if (okp) okp = f.reuse ? (e >= ncol || cc < e) : (vi != vj);
             T I = T(0);
@@ -1055,7 +1106,7 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
         __syncthreads();
         if (sh.flag) {
             __threadfence();
-            wave_finalize<CONS, TI, TJ>(f, it, sh.red);
+            wave_finalize<CONS, TI, TJ>(f, wv, it, sh.red);
         }
         __syncthreads();
     }
