@@ -63,8 +63,8 @@ struct Ctl {
     int merged;          // tiles of the current wave merged so far
     long long pairs_it;  // pairs evaluated this iteration
     unsigned long long timeout_ns;  // bound on device-side waits
-    int bar_count;       // grid barrier: CTAs arrived
-    int bar_gen;         // grid barrier: generation
+    unsigned bar_count;  // grid barrier: arrivals since the fit started (never reset)
+    int pad0;
     int abort;           // set when a CTA gives up a wait; the others then leave too
     int pad1;
     unsigned long long phase_ns[3];   // with timing: pair compute, merge + finalise, removal (CTA 0)

@@ -208,39 +208,44 @@ __device__ __forceinline__ void load16_cg(double* v, const double* src) {
     }
 }
 
-// Grid-wide barrier (sense by generation count), bounded: returns false when this
-// CTA gave up (timeout, recorded) or another CTA did (ctl->abort).
+// Grid-wide barrier, bounded: returns false when this CTA gave up (timeout, recorded)
+// or another CTA did (ctl->abort).  The arrival count only grows: it is zero when a
+// fit starts and every CTA of a launch arrives once per barrier, so the arrivals at a
+// barrier are those numbered [k G, (k + 1) G) for a grid of G CTAs, and a CTA waits
+// until the count reaches the end of its block.  One atomic and one polling load per
+// CTA; the abort flag is read by the same polls.
 __device__ bool grid_sync(Ctl* ctl, unsigned long long tmo) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile int* genp = &ctl->bar_gen;
-        volatile int* abortp = &ctl->abort;
-        const int gen = *genp;
+        const unsigned G = gridDim.x;
         __threadfence();
-        if (atomicAdd(&ctl->bar_count, 1) == int(gridDim.x) - 1) {
-            ctl->bar_count = 0;
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1);
-        } else {
-            const unsigned long long t0 = global_ns();
-            while (*genp == gen) {
-                if (*abortp) {
-                    ok = 0;
-                    break;
-                }
-                if (global_ns() - t0 > tmo) {
-                    set_status(ctl, LINGAM_ETIMEOUT);
-                    ctl->abort = 1;
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        const unsigned old = atomicAdd(&ctl->bar_count, 1u);
+        const unsigned target = old - old % G + G;
+        volatile unsigned* cntp = &ctl->bar_count;
+        volatile int* abortp = &ctl->abort;
+        unsigned long long t0 = 0;
+        for (;;) {
+            const unsigned c = *cntp;
+            const int ab = *abortp;
+            if (ab) {
+                ok = 0;
+                break;
+            }
+            if (int(c - target) >= 0) break;
+            const unsigned long long now = global_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > tmo) {
+                set_status(ctl, LINGAM_ETIMEOUT);
+                ctl->abort = 1;
+                ok = 0;
+                break;
             }
         }
         __threadfence();
-        s_ok = ok && !*abortp;
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
