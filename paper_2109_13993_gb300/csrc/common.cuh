@@ -54,10 +54,8 @@ struct Ctl {
     int wave;            // wave counter within the iteration
     int ncol;            // columns of the current wave
     int nrow;            // rows of the current wave (columns first, then the rest)
-    int wave_ctas_done;  // CTAs of the current wave that have finished
     int ntiles;          // row tiles of the current wave
-    int nsplit;          // sample splits of the current wave
-    int ncolumned;       // variables that have been a column this iteration
+    int pad2;
     double best;         // lowest complete score so far this iteration
     int best_var;        // variable holding `best`
     int merged;          // tiles of the current wave merged so far
@@ -68,7 +66,17 @@ struct Ctl {
     int abort;           // set when a CTA gives up a wait; the others then leave too
     int pad1;
     unsigned long long phase_ns[3];   // with timing: pair compute, merge + finalise, removal (CTA 0)
+    // the next wave as published by the wave finalisation of a single fit: sequence
+    // number within the iteration (bits 49-63), done (bit 48), tiles (32-47), columns
+    // (24-31), rows (0-23); zero when the iteration is planned
+    unsigned long long wave_word;
 };
+
+__host__ __device__ inline unsigned long long pack_wave(unsigned seq, int done, int ntiles, int ncol, int nrow) {
+    return (static_cast<unsigned long long>(seq & 0x7fffu) << 49) | (static_cast<unsigned long long>(done & 1) << 48) |
+           (static_cast<unsigned long long>(ntiles & 0xffff) << 32) | (static_cast<unsigned long long>(ncol & 0xff) << 24) |
+           static_cast<unsigned long long>(nrow & 0xffffff);
+}
 
 // Where a batch problem's samples come from: row i of the problem is the row of
 // x with stride ld (elements of the input type), sample t at column t, or at

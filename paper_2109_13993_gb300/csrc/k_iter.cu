@@ -372,6 +372,7 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
         ctl->best = INFINITY;
         ctl->best_var = -1;
         ctl->pairs_it = 0;
+        ctl->wave_word = 0;
         if (r <= 1) {
             // Algorithm 2: a single remaining variable is the root
             const int root = r == 1 ? f.sigma[0] : -1;
@@ -404,7 +405,7 @@ struct Wave {
 
 // Run by one CTA (the one that merged the wave's last tile).
 template <int NTH, int TI, int TJ>
-__device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it, int* red) {
+__device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it, int* red, unsigned seq) {
     Ctl* ctl = f.ctl;
     volatile Ctl* vc = ctl;
     const int tid = threadIdx.x;
@@ -634,7 +635,9 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
             f.inv_root[w] = 1.0 / sqrt(om);
         }
     }
+    __syncthreads();   // every thread's writes precede the publication below
     if (tid == 0) {
+        const int ntiles_next = (nc + nr + TI - 1) / TI;
         if (nc == 0) {
             ctl->root = root;
             ctl->done = 1;
@@ -645,10 +648,16 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
         } else {
             ctl->ncol = nc;
             ctl->nrow = nc + nr;
-            ctl->ntiles = (nc + nr + TI - 1) / TI;
+            ctl->ntiles = ntiles_next;
             ctl->wave += 1;
         }
         ctl->merged = 0;
+        if (seq != 0) {
+            // publish: the CTAs of a single fit wait for this word instead of a grid barrier
+            __threadfence();
+            *reinterpret_cast<volatile unsigned long long*>(&ctl->wave_word) =
+                pack_wave(seq, nc == 0, nc == 0 ? 0 : ntiles_next, nc, nc + nr);
+        }
     }
 }
 
@@ -992,7 +1001,7 @@ __device__ __noinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wave& 
 // last tile runs the wave finalisation.
 template <class Cfg>
 __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span& sp, int it, IterShared& sh,
-                                        typename Cfg::T* scratch, int item) {
+                                        typename Cfg::T* scratch, int item, unsigned seq) {
     using T = typename Cfg::T;
     constexpr int TI = Cfg::TI, TJ = Cfg::TJ, CONS = Cfg::CONS;
     constexpr int NW = CONS / 32;
@@ -1111,7 +1120,7 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
         __syncthreads();
         if (sh.flag) {
             __threadfence();
-            wave_finalize<CONS, TI, TJ>(f, wv, it, sh.red);
+            wave_finalize<CONS, TI, TJ>(f, wv, it, sh.red, seq);
         }
         __syncthreads();
     }
@@ -1120,9 +1129,10 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
 // The merge of one problem's wave: its items spread over the CTAs.
 template <class Cfg>
 __device__ __forceinline__ void merge_phase(const Fit& f, const Wave& wv, const Span& sp, int it, IterShared& sh,
-                                            typename Cfg::T* scratch) {
+                                            typename Cfg::T* scratch, unsigned seq) {
     const int nitems = wv.ntiles * (Cfg::CONS / 64);
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x) merge_item<Cfg>(f, wv, sp, it, sh, scratch, item);
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x)
+        merge_item<Cfg>(f, wv, sp, it, sh, scratch, item, seq);
 }
 
 // ------------------------------------------------------------------ removal phases
@@ -1248,6 +1258,50 @@ __device__ __noinline__ void remove_cov_phase(const Fit& f, int vb, int vG) {
 }
 
 // ------------------------------------------------------------------ the iteration kernel
+// Wait (bounded) until the wave finalisation of a single fit has published wave word
+// seq; returns the next wave and whether the iteration is done.  Returns false when
+// this CTA gave up (timeout, recorded) or another CTA did.
+__device__ bool wait_wave(Ctl* ctl, unsigned seq, unsigned long long tmo, Wave& wv, bool& done) {
+    __shared__ unsigned long long s_word;
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned long long* wp = &ctl->wave_word;
+        volatile int* abortp = &ctl->abort;
+        unsigned long long w = 0, t0 = 0;
+        for (;;) {
+            w = *wp;
+            const int ab = *abortp;
+            if (ab) {
+                ok = 0;
+                break;
+            }
+            if (unsigned(w >> 49) == (seq & 0x7fffu)) break;
+            const unsigned long long now = global_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > tmo) {
+                set_status(ctl, LINGAM_ETIMEOUT);
+                ctl->abort = 1;
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        s_word = w;
+        s_ok = ok;
+    }
+    __syncthreads();
+    const unsigned long long w = s_word;
+    const int ok = s_ok;
+    __syncthreads();   // s_word and s_ok are reused by the next wait
+    done = ((w >> 48) & 1) != 0;
+    wv.ntiles = int((w >> 32) & 0xffff);
+    wv.ncol = int((w >> 24) & 0xff);
+    wv.nrow = int(w & 0xffffff);
+    return ok != 0;
+}
+
 template <class Cfg>
 __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int it) {
     unsigned char* smem_raw = smem_dyn;
@@ -1280,8 +1334,10 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
     // grid barriers, so each interval covers the slowest CTA of the phase
     const bool timed = f.timing && blockIdx.x == 0 && threadIdx.x == 0;
     unsigned long long tph = timed ? global_ns() : 0;
-    while (!vc->done) {
-        const Wave wv = {vc->ntiles, vc->ncol, vc->nrow};
+    // the first wave as planned; later ones as published by each wave's finalisation
+    Wave wv = {vc->ntiles, vc->ncol, vc->nrow};
+    bool done = vc->done != 0;
+    for (unsigned seq = 1; !done; ++seq) {
         const Span sp = single_span((long long)wv.ntiles * (f.ld / kSub), gridDim.x);
         if (!compute_phase<Cfg>(f, ctl, wv, sp, ring, full, empty, sh, chunk_base)) {
             ctl->abort = 1;
@@ -1293,9 +1349,11 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
             ctl->phase_ns[0] += t - tph;
             tph = t;
         }
-        merge_phase<Cfg>(f, wv, sp, it, sh, ring);
+        merge_phase<Cfg>(f, wv, sp, it, sh, ring, seq);
         fence_proxy_async();   // the merge used the copy ring as scratch
-        if (!grid_sync(ctl, tmo)) return;
+        // the wave's finalisation runs after every merge item, so its published word also
+        // tells that every CTA is done with this wave's partial moments
+        if (!wait_wave(ctl, seq, tmo, wv, done)) return;
         if (timed) {
             const unsigned long long t = global_ns();
             ctl->phase_ns[1] += t - tph;
@@ -1477,7 +1535,7 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
             for (int gi = blockIdx.x; gi < itot; gi += gridDim.x) {
                 const int d = last_le(bs.ioff, count, gi);
                 const Span sp{bs.uoff[d], utot, G, cta_of_unit(bs.uoff[d], utot, G)};
-                merge_item<Cfg>(fits[d], bs.wave[d], sp, it, sh, ring, gi - bs.ioff[d]);
+                merge_item<Cfg>(fits[d], bs.wave[d], sp, it, sh, ring, gi - bs.ioff[d], 0u);
             }
             fence_proxy_async();   // the merge used the copy ring as scratch
             if (!grid_sync(bctl, tmo)) return;
