@@ -748,7 +748,7 @@ __device__ __forceinline__ Span single_span(long long U, long long Gmax) {
 }
 
 template <class Cfg>
-__device__ __noinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wave& wv, const Span& sp,
+__device__ __forceinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wave& wv, const Span& sp,
                                            typename Cfg::T* ring, uint64_t* full, uint64_t* empty, IterShared& sh,
                                            int& chunk_base) {
     using T = typename Cfg::T;
