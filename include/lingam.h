@@ -174,6 +174,20 @@ int lingam_autotune(const void* X, long long p, long long n, void* workspace, co
                     int* tile_rows, int* tile_cols, double* ms);
 void lingam_autotune_reset(void);
 
+/*
+ * lingam_selftest_wait -- failure detection check: one of the device-side waits of the
+ * iteration kernel, made to wait for an event that never happens, must give up after
+ * timeout_s seconds and record LINGAM_ETIMEOUT in its control block, and the kernel must
+ * end normally (the context stays usable).  which = 0: an mbarrier phase that no thread
+ * completes (the copy-ring waits); 1: the grid barrier with its arrival count started one
+ * arrival off (two CTAs); 2: the wave word of a single fit that nothing publishes.  The
+ * control block is a library-owned device variable.  *observed receives the recorded
+ * status.  Returns LINGAM_EINVAL for which outside 0..2, timeout_s outside (0, 60] or a
+ * NULL observed, LINGAM_ECUDA if the launch fails, else LINGAM_OK.  Synchronous on the
+ * legacy default stream.
+ */
+int lingam_selftest_wait(int which, double timeout_s, int* observed);
+
 /* Workspace for lingam_fit_batch over `count` datasets of sizes p[k] x n[k]. */
 size_t lingam_workspace_size_batch(int count, const long long* p, const long long* n, const lingam_opts* opts);
 

@@ -1617,4 +1617,52 @@ cudaError_t launch_batch(const Fit* fits_dev, int count, int maxp, int precision
                                      : launch_batch_cfg<CfgD>(fits_dev, count, maxp, bctl, nsm, st);
 }
 
+// ------------------------------------------------------------------ bounded-wait self-test
+// Each of the iteration kernel's three kinds of wait, made to wait for something that never
+// happens, must give up after the control block's timeout with LINGAM_ETIMEOUT recorded and
+// let the kernel end normally: which = 0, an mbarrier phase that no thread completes (the
+// copy-ring waits); 1, a grid barrier whose arrival count starts one off, so that the second
+// of two CTAs waits for an arrival that never comes; 2, a wave word that nothing publishes.
+// No copies or tensor-memory allocations are in flight in this kernel.
+__device__ Ctl g_selftest_ctl;
+
+__global__ void k_wait_selftest(int which) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_abort;
+    Ctl* ctl = &g_selftest_ctl;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        s_abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const unsigned long long tmo = *reinterpret_cast<volatile unsigned long long*>(&ctl->timeout_ns);
+    if (which == 0) {
+        mbar_wait_or_abort(&bar, 0, ctl, tmo, &s_abort);
+    } else if (which == 1) {
+        grid_sync(ctl, tmo);
+    } else {
+        Wave wv;
+        bool done = false;
+        wait_wave(ctl, 1u, tmo, wv, done);
+    }
+}
+
+cudaError_t run_wait_selftest(int which, unsigned long long timeout_ns, int* status, cudaStream_t st) {
+    Ctl h = {};
+    h.timeout_ns = timeout_ns;
+    if (which == 1) h.bar_count = 1;   // one arrival off: the second CTA's block never fills
+    cudaError_t e = cudaMemcpyToSymbolAsync(g_selftest_ctl, &h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    k_wait_selftest<<<which == 1 ? 2 : 1, 32, 0, st>>>(which);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyFromSymbolAsync(&h, g_selftest_ctl, sizeof(h), 0, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    *status = h.status;
+    return cudaSuccess;
+}
+
 }  // namespace lingam

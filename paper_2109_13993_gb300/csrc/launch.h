@@ -41,6 +41,8 @@ cudaError_t launch_batch(const Fit* fits_dev, int count, int maxp, int precision
 constexpr int kBatchLaunchMax = 512;   // problems per launch_batch
 // B from the order: Cholesky of the covariance in causal order, B = I - diag(R) R^{-1}.
 cudaError_t launch_fit_B(const Fit& f, cudaStream_t st);
+// Bounded-wait self-test (k_iter.cu): the status the wait recorded (LINGAM_ETIMEOUT expected).
+cudaError_t run_wait_selftest(int which, unsigned long long timeout_ns, int* status, cudaStream_t st);
 // B of many problems: one CTA per problem of p <= 128 (shared-memory Cholesky), the
 // multi-launch fit for larger ones.  p_host and fits_host mirror the device table.
 cudaError_t launch_fit_B_batch(const Fit* fits_dev, const int* p_host, int count, const Fit* fits_host,

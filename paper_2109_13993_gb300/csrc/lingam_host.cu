@@ -862,6 +862,17 @@ int lingam_fit_bootstrap(const void* X, long long p, long long n, int nboot, con
     return fit_many(items, workspace, o, status, &boot);
 }
 
+int lingam_selftest_wait(int which, double timeout_s, int* observed) {
+    if (which < 0 || which > 2 || !(timeout_s > 0.0) || timeout_s > 60.0 || !observed) return LINGAM_EINVAL;
+    int st = 0;
+    if (run_wait_selftest(which, (unsigned long long)(timeout_s * 1e9), &st, nullptr) != cudaSuccess) {
+        cudaGetLastError();
+        return LINGAM_ECUDA;
+    }
+    *observed = st;
+    return LINGAM_OK;
+}
+
 const char* lingam_status_string(int s) {
     switch (s) {
         case LINGAM_OK: return "ok";

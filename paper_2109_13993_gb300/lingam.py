@@ -101,6 +101,8 @@ def load():
     L.lingam_autotune_reset.restype = None
     L.lingam_status_string.argtypes = [ctypes.c_int]
     L.lingam_status_string.restype = ctypes.c_char_p
+    L.lingam_selftest_wait.argtypes = [ctypes.c_int, ctypes.c_double, _c_int_p]
+    L.lingam_selftest_wait.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -299,6 +301,16 @@ def autotune(X, stream=None, workspace=None):
 
 def autotune_reset():
     load().lingam_autotune_reset()
+
+
+def selftest_wait(which: int, timeout_s: float) -> int:
+    """lingam_selftest_wait: the status one device-side wait recorded after waiting for an
+    event that never happens (0: mbarrier phase, 1: grid barrier, 2: wave word)."""
+    obs = ctypes.c_int(0)
+    st = load().lingam_selftest_wait(int(which), float(timeout_s), ctypes.byref(obs))
+    if st != LINGAM_OK:
+        raise LingamError(st, status_string(st))
+    return int(obs.value)
 
 
 def _reports(count, ps, want_report):

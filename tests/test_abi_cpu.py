@@ -111,3 +111,13 @@ def test_batch_rejects_bad_arguments_without_gpu_work(lib):
     assert lib.lingam_fit_bootstrap(ctypes.c_void_p(x.ctypes.data), 3, 10, 2, ctypes.c_void_p(idx.ctypes.data),
                                     ctypes.c_void_p(o2.ctypes.data), None, ctypes.c_void_p(ws.ctypes.data), None,
                                     None, None) == lingam.LINGAM_EINVAL
+
+
+def test_selftest_wait_rejects_bad_arguments_without_gpu_work(lib):
+    obs = ctypes.c_int(-7)
+    assert lib.lingam_selftest_wait(3, 0.05, ctypes.byref(obs)) == lingam.LINGAM_EINVAL
+    assert lib.lingam_selftest_wait(-1, 0.05, ctypes.byref(obs)) == lingam.LINGAM_EINVAL
+    assert lib.lingam_selftest_wait(0, 0.0, ctypes.byref(obs)) == lingam.LINGAM_EINVAL
+    assert lib.lingam_selftest_wait(0, 120.0, ctypes.byref(obs)) == lingam.LINGAM_EINVAL
+    assert lib.lingam_selftest_wait(0, 0.05, None) == lingam.LINGAM_EINVAL
+    assert obs.value == -7
