@@ -1382,9 +1382,13 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
 constexpr int kBatchMax = kBatchLaunchMax;   // problems per launch
 
 struct BatchShared {
-    long long uoff[kBatchMax + 1];   // first unit of each problem in this wave (prefix)
-    int ioff[kBatchMax + 1];         // first merge item of each problem in this wave
+    long long uoff[kBatchMax + 1];   // first unit of each problem in this wave (prefix);
+                                     // removal: first covariance element of each problem
+    int ioff[kBatchMax + 1];         // first merge item of each problem in this wave;
+                                     // removal: first row of each problem
     Wave wave[kBatchMax];            // each problem's wave, read at the wave's start
+    int rr[kBatchMax];               // removal: rows of U (r) of each problem
+    int root[kBatchMax];             // removal: each problem's root
     unsigned char act[kBatchMax];    // per problem: take part in this phase (one read per CTA)
 };
 
@@ -1482,6 +1486,135 @@ __device__ __forceinline__ int last_le(const I* off, int count, long long v) {
     return lo;
 }
 
+// The removal of every problem that took a root, spread over the whole grid at once (a
+// CTA that walked the problems one after another would pay each problem's latency): the
+// rows of U of all problems are numbered one after another, and so are the elements of
+// their covariance blocks.  Every CTA computes the same numbering from the problems'
+// control blocks, which the removal does not change.
+template <int NTH>
+__device__ void batch_removal_layout(const Fit* fits, int count, BatchShared& bs, IterShared& sh, int& rtot,
+                                     long long& etot) {
+    long long rbase = 0, ebase = 0;
+    for (int base = 0; base < count; base += NTH) {
+        const int d = base + int(threadIdx.x);
+        long long rows = 0, elems = 0;
+        if (d < count) {
+            int r = 0, root = -1;
+            if (bs.act[d]) {
+                volatile Ctl* c = fits[d].ctl;
+                r = c->r;
+                root = c->root;
+            }
+            bs.rr[d] = r;
+            bs.root[d] = root;
+            rows = r;
+            elems = (long long)r * r;
+        }
+        long long tr, te;
+        const long long er = block_excl_scan<NTH>(rows, sh.lred, &tr);
+        const long long ee = block_excl_scan<NTH>(elems, sh.lred, &te);
+        if (d < count) {
+            bs.ioff[d] = int(rbase + er);
+            bs.uoff[d] = ebase + ee;
+        }
+        rbase += tr;
+        ebase += te;
+    }
+    if (threadIdx.x == 0) {
+        bs.ioff[count] = int(rbase);
+        bs.uoff[count] = ebase;
+    }
+    __syncthreads();
+    rtot = int(rbase);
+    etot = ebase;
+}
+
+// UpdateData (Algorithm 7) with the new H(x_w), one warp per row of any problem: lanes
+// take float4 (FP32 path) or single samples, sum the moments in the working precision in
+// blocks of 8 steps, flushed into FP64, and the warp tree is FP64.
+template <class Cfg>
+__device__ __noinline__ void batch_remove_data(const Fit* fits, int count, const BatchShared& bs, int rtot) {
+    using T = typename Cfg::T;
+    constexpr int NW = Cfg::CONS / 32;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * NW + (threadIdx.x >> 5), GW = gridDim.x * NW;
+    for (int i = gw; i < rtot; i += GW) {
+        const int d = last_le(bs.ioff, count, i);
+        const Fit& f = fits[d];
+        const int root = bs.root[d], p = f.p, ld = f.ld, n = f.n;
+        const int w = ld2(f.sigma + (i - bs.ioff[d]));
+        if (w == root) continue;
+        const double c = f.sig[size_t(root) * p + w], inv = ld2(f.inv_root + w);
+        T* xw = static_cast<T*>(f.xt) + size_t(w) * ld;
+        const T* xr = static_cast<const T*>(f.xt) + size_t(root) * ld;
+        double L = 0.0, Gs = 0.0;
+        if constexpr (std::is_same<T, float>::value) {
+            const float cc = float(c), ii = float(inv);
+            float4* xw4 = reinterpret_cast<float4*>(xw);
+            const float4* xr4 = reinterpret_cast<const float4*>(xr);
+            const int n4 = ld / 4;
+            for (int b0 = lane; b0 < n4; b0 += 32 * 8) {
+                float lcc = 0.f, g = 0.f;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int t4 = b0 + 32 * q;
+                    if (t4 < n4) {
+                        const float4 a = xw4[t4], rr = xr4[t4];
+                        float4 o;
+                        o.x = fmaf(-cc, rr.x, a.x) * ii;
+                        o.y = fmaf(-cc, rr.y, a.y) * ii;
+                        o.z = fmaf(-cc, rr.z, a.z) * ii;
+                        o.w = fmaf(-cc, rr.w, a.w) * ii;
+                        xw4[t4] = o;   // padding samples stay exactly zero
+                        const int t = 4 * t4;
+                        if (t + 0 < n) mom_add(o.x, lcc, g);
+                        if (t + 1 < n) mom_add(o.y, lcc, g);
+                        if (t + 2 < n) mom_add(o.z, lcc, g);
+                        if (t + 3 < n) mom_add(o.w, lcc, g);
+                    }
+                }
+                L += double(lcc);
+                Gs += double(g);
+            }
+        } else {
+            for (int t = lane; t < ld; t += 32) {
+                const double u = fma(-c, xr[t], xw[t]) * inv;
+                xw[t] = u;
+                if (t < n) mom_add(u, L, Gs);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            L += __shfl_xor_sync(0xffffffffu, L, o);
+            Gs += __shfl_xor_sync(0xffffffffu, Gs, o);
+        }
+        if (lane == 0) f.hx[w] = hterm(L, Gs, double(n));
+    }
+}
+
+// UpdateCovMat (Algorithm 8 / Eq. CovUpdate) in FP64, one thread per element (w, j) of
+// any problem's block of U without its root.
+template <class Cfg>
+__device__ __noinline__ void batch_remove_cov(const Fit* fits, int count, const BatchShared& bs, long long etot) {
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x, GT = (long long)gridDim.x * blockDim.x;
+    for (long long e = gt; e < etot; e += GT) {
+        const int d = last_le(bs.uoff, count, e);
+        const Fit& f = fits[d];
+        const int r = bs.rr[d], root = bs.root[d], p = f.p;
+        const long long loc = e - bs.uoff[d];
+        const int kk = int(loc / r), jj = int(loc - (long long)kk * r);
+        const int w = ld2(f.sigma + kk), j = ld2(f.sigma + jj);
+        if (w == root || j == root) continue;
+        double* row = f.sig + size_t(w) * p;
+        if (j == w) {
+            row[j] = 1.0;
+        } else {
+            const double* rootrow = f.sig + size_t(root) * p;
+            row[j] = (row[j] - rootrow[w] * rootrow[j]) * (ld2(f.inv_root + w) * ld2(f.inv_root + j));
+        }
+    }
+}
+
 template <class Cfg>
 __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __restrict__ fits, int count, int maxp,
                                                                Ctl* bctl) {
@@ -1540,15 +1673,15 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
             fence_proxy_async();   // the merge used the copy ring as scratch
             if (!grid_sync(bctl, tmo)) return;
         }
-        // UpdateData and UpdateCovMat of every problem that took a root.  Problem d's rows
-        // start at CTA (97 d) mod grid, a rotation fixed by d alone, so that every CTA
-        // agrees on the partition and the rows of many problems spread over the grid.
+        // UpdateData and UpdateCovMat of every problem that took a root, all problems' rows
+        // and covariance elements spread over the grid at once (disjoint memory: the root's
+        // row and column, from which the coefficients come, are not written)
         batch_active(fits, count, it, 1, bs);
-        for (int d = 0; d < count; ++d)
-            if (bs.act[d])
-                remove_data_phase<Cfg>(fits[d], sh, int((blockIdx.x + 97ull * d) % gridDim.x), gridDim.x);
-        for (int d = 0; d < count; ++d)
-            if (bs.act[d]) remove_cov_phase<Cfg>(fits[d], int((blockIdx.x + 97ull * d) % gridDim.x), gridDim.x);
+        int rtot;
+        long long etot;
+        batch_removal_layout<CONS>(fits, count, bs, sh, rtot, etot);
+        batch_remove_data<Cfg>(fits, count, bs, rtot);
+        batch_remove_cov<Cfg>(fits, count, bs, etot);
         if (!grid_sync(bctl, tmo)) return;
     }
 }
