@@ -1389,6 +1389,8 @@ struct BatchShared {
     Wave wave[kBatchMax];            // each problem's wave, read at the wave's start
     int rr[kBatchMax];               // removal: rows of U (r) of each problem
     int root[kBatchMax];             // removal: each problem's root
+    int fin[kBatchMax];              // merge: problems whose last item this CTA merged
+    int nfin;
     unsigned char act[kBatchMax];    // per problem: take part in this phase (one read per CTA)
 };
 
@@ -1484,6 +1486,128 @@ __device__ __forceinline__ int last_le(const I* off, int count, long long v) {
         else hi = mid - 1;
     }
     return lo;
+}
+
+// Batches on the FP32 path: the merge items of all problems, one warp per item.  A batch's
+// tiles are shared by few CTAs each, so an item has few partial slots and a CTA-wide item
+// would mostly wait on its round trips; here sixteen items per CTA proceed at once.  The
+// arithmetic and its order are those of merge_item: the slots b_first + w, + NW, ... of
+// each "virtual warp" w are summed in order, those sums in w order; lane L holds the
+// values of the item's pairs 8 L ... 8 L + 7.  The warp that merges a problem's last item
+// records the problem, and the CTA then runs those problems' wave finalisations.
+template <class Cfg>
+__device__ __noinline__ void batch_merge_warps(const Fit* fits, int count, BatchShared& bs, long long utot,
+                                               long long G, int itot, int it, IterShared& sh, float* scratch) {
+    constexpr int TI = Cfg::TI, TJ = Cfg::TJ, CONS = Cfg::CONS;
+    constexpr int NW = CONS / 32, PARTS = CONS / 64;
+    constexpr int HJ = TJ / 2, IR = 2 * (64 / HJ);   // rows of an item
+    static_assert(std::is_same<typename Cfg::T, float>::value, "FP32 path");
+    static_assert(IR <= 32 && TJ <= 32, "an item's rows and columns are lanes");
+    static_assert(size_t(NW) * IR * (TJ + 1) * sizeof(float) <= ring_bytes<Cfg>(), "staging fits the ring");
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float* sI = scratch + wid * (IR * (TJ + 1));
+    if (threadIdx.x == 0) bs.nfin = 0;
+    __syncthreads();
+    // Many items (at least half a warp each): consecutive items to the warps of a CTA (a
+    // problem's items and finalisation stay together); fewer: item gi to warp gi / grid of
+    // CTA gi mod grid, spread over all CTAs first.  The choice depends on itot alone.
+    const bool blocked = itot >= int(gridDim.x) * NW / 2;
+    for (int gi = blocked ? int(blockIdx.x) * NW + wid : wid * int(gridDim.x) + int(blockIdx.x); gi < itot;
+         gi += gridDim.x * NW) {
+        const int d = last_le(bs.ioff, count, gi);
+        const Fit& f = fits[d];
+        Ctl* ctl = f.ctl;
+        const Wave wv = bs.wave[d];
+        const int ncol = wv.ncol, nrow = wv.nrow;
+        const long long off = bs.uoff[d];
+        const int b_base = cta_of_unit(off, utot, G);
+        const int item = gi - bs.ioff[d];
+        const int t = item / PARTS, part = item % PARTS;
+        const long long ng = f.ld / kSub;
+        const int b_first = cta_of_unit(off + (long long)t * ng, utot, G) - b_base;
+        const int b_last = cta_of_unit(off + (long long)(t + 1) * ng - 1, utot, G) - b_base;
+        // this lane's pairs 8 lane + j: their rows, columns and variables
+        int vi[8], vj[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int tp = 8 * lane + j;
+            const int ct = part * 64 + (tp >> 2), q = tp & 3;
+            const int e = t * TI + ct / HJ + (q >> 1) * (TI / 2), cc = ct % HJ + (q & 1) * HJ;
+            vi[j] = e < nrow ? ld2(f.rows + e) : -1;
+            vj[j] = cc < ncol ? ld2(f.cols + cc) : -1;
+        }
+        // 1. the item's 1024 values, 32 per lane, over its slots
+        const float* parts = static_cast<const float*>(f.partials);
+        float acc[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc[k] = 0.f;
+        for (int w = 0; w < NW; ++w) {
+            int bb = b_first + w;
+            if (bb > b_last) continue;   // an empty virtual warp adds +0: no change
+            float vs[32];
+            {
+                const float* src = parts + ((size_t(t) + bb) * CONS + part * 64) * 16 + lane * 32;
+                load16_cg(vs, src);
+                load16_cg(vs + 16, src + 16);
+            }
+            for (bb += NW; bb <= b_last; bb += NW) {
+                const float* src = parts + ((size_t(t) + bb) * CONS + part * 64) * 16 + lane * 32;
+                float v[32];
+                load16_cg(v, src);
+                load16_cg(v + 16, src + 16);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) vs[k] += v[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 32; ++k) acc[k] += vs[k];
+        }
+        // 2. I of the lane's 8 pairs, staged by (item row, column)
+        const double n = double(f.n);
+        const double pad_fix = double(f.ld - f.n) * kBeta;
+        const float inv_n = float(1.0 / n);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int tp = 8 * lane + j;
+            const int ct = part * 64 + (tp >> 2), q = tp & 3;
+            const int e = t * TI + ct / HJ + (q >> 1) * (TI / 2), cc = ct % HJ + (q & 1) * HJ;
+            bool okp = vi[j] >= 0 && vj[j] >= 0;
+            if (okp) okp = f.reuse ? (e >= ncol || cc < e) : (vi[j] != vj[j]);
+            float I = 0.f;
+            if (okp) {
+                const float ha = hterm_f(acc[4 * j + 0] + float(pad_fix), acc[4 * j + 1] * kInvScale, inv_n);
+                const float hb = hterm_f(acc[4 * j + 2] + float(pad_fix), acc[4 * j + 3] * kInvScale, inv_n);
+                I = (float(f.hx[vj[j]]) - float(f.hx[vi[j]])) + (ha - hb);
+                if (!isfinite(double(I))) set_status(ctl, LINGAM_EDEGENERATE);
+            }
+            const int el = ct / HJ - part * (64 / HJ) + (q >> 1) * (64 / HJ);
+            sI[el * (TJ + 1) + cc] = I;
+        }
+        __syncwarp();
+        // 3. the item's rows' contributions over all columns, and its part of each column's
+        if (lane < IR) {
+            const int e = t * TI + (lane < IR / 2 ? part * (IR / 2) + lane : part * (IR / 2) + lane - IR / 2 + TI / 2);
+            FF a;
+            for (int cc = 0; cc < TJ; ++cc) a.add_sq(fminf(sI[lane * (TJ + 1) + cc], 0.f));
+            if (e < nrow) f.rowsum[e] = a.value();
+        }
+        if (lane < TJ) {
+            FF a;
+            for (int el = 0; el < IR; ++el) a.add_sq(fmaxf(sI[el * (TJ + 1) + lane], 0.f));
+            f.colsum[(size_t(t) * PARTS + part) * TJ + lane] = a.value();
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0 && atomicAdd(&ctl->merged, 1) == wv.ntiles * PARTS - 1) bs.fin[atomicAdd(&bs.nfin, 1)] = d;
+        __syncwarp();   // sI is staged again by the next item
+    }
+    __syncthreads();
+    const int nfin = bs.nfin;
+    for (int k = 0; k < nfin; ++k) {
+        const int d = bs.fin[k];
+        __threadfence();
+        wave_finalize<CONS, TI, TJ>(fits[d], bs.wave[d], it, sh.red, 0u);
+        __syncthreads();
+    }
 }
 
 // The removal of every problem that took a root, spread over the whole grid at once (a
@@ -1665,10 +1789,14 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
                 }
             }
             if (!grid_sync(bctl, tmo)) return;
-            for (int gi = blockIdx.x; gi < itot; gi += gridDim.x) {
-                const int d = last_le(bs.ioff, count, gi);
-                const Span sp{bs.uoff[d], utot, G, cta_of_unit(bs.uoff[d], utot, G)};
-                merge_item<Cfg>(fits[d], bs.wave[d], sp, it, sh, ring, gi - bs.ioff[d], 0u);
+            if constexpr (std::is_same<T, float>::value) {
+                batch_merge_warps<Cfg>(fits, count, bs, utot, G, itot, it, sh, ring);
+            } else {
+                for (int gi = blockIdx.x; gi < itot; gi += gridDim.x) {
+                    const int d = last_le(bs.ioff, count, gi);
+                    const Span sp{bs.uoff[d], utot, G, cta_of_unit(bs.uoff[d], utot, G)};
+                    merge_item<Cfg>(fits[d], bs.wave[d], sp, it, sh, ring, gi - bs.ioff[d], 0u);
+                }
             }
             fence_proxy_async();   // the merge used the copy ring as scratch
             if (!grid_sync(bctl, tmo)) return;
