@@ -207,7 +207,7 @@ size_t lingam_workspace_size_batch(int count, const long long* p, const long lon
  * graph on the second call with the same workspace and problem shapes (and options),
  * and replayed by every later such call; calls on the legacy default stream (NULL)
  * run without a graph.  opts->forced_order must be NULL and opts->max_iters 0; the
- * pair tiles have 64 rows (mixed) or 32 (FP64).
+ * pair tiles are 32 x 32 on both paths.
  */
 int lingam_fit_batch(int count, const void* const* X, const long long* p, const long long* n, int* const* order,
                      double* const* B, void* workspace, const lingam_opts* opts, int* status,

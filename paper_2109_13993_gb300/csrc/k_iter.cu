@@ -1874,7 +1874,7 @@ static cudaError_t launch_batch_cfg(const Fit* fits_dev, int count, int maxp, Ct
 cudaError_t launch_batch(const Fit* fits_dev, int count, int maxp, int precision, Ctl* bctl, int nsm,
                          cudaStream_t st) {
     if (count < 1 || count > kBatchMax) return cudaErrorInvalidValue;
-    return precision == LINGAM_MIXED ? launch_batch_cfg<CfgF64>(fits_dev, count, maxp, bctl, nsm, st)
+    return precision == LINGAM_MIXED ? launch_batch_cfg<CfgF32>(fits_dev, count, maxp, bctl, nsm, st)
                                      : launch_batch_cfg<CfgD>(fits_dev, count, maxp, bctl, nsm, st);
 }
 

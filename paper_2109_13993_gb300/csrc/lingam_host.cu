@@ -602,7 +602,7 @@ static int fit_many(std::vector<BatchItem>& items, void* workspace, const lingam
         const Layout& L = Ls[size_t(k)];
         Fit f = make_fit(base, L, int(it.p), int(it.n), o, it.rep && it.rep->scores);
         f.ctl = reinterpret_cast<Ctl*>(ws + BL.off_ctls) + k;
-        f.tile_rows = o.precision == LINGAM_MIXED ? 64 : 32;   // the batch kernel's tile shape
+        f.tile_rows = 32;   // the batch kernel's tile shape (32 x 32 on both paths)
         f.tile_cols = 32;
         fits[size_t(k)] = f;
         SrcDesc sd;

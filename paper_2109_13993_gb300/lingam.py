@@ -393,7 +393,7 @@ def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = T
 
 
 def fit_bootstrap(X, idx, precision: str = "mixed", prune: bool = True, want_B: bool = True, stream=None,
-                  workspace=None) -> BatchResult:
+                  workspace=None, want_report: bool = False) -> BatchResult:
     """lingam_fit_bootstrap: X (p x n), idx (nboot x n column indices, numpy or CUDA tensor)."""
     L = load()
     torch = _torch()
@@ -417,11 +417,17 @@ def fit_bootstrap(X, idx, precision: str = "mixed", prune: bool = True, want_B: 
     order = np.zeros((nboot, p), dtype=np.int32)
     B = np.zeros((nboot, p, p)) if want_B else None
     status = np.zeros(nboot, dtype=np.int32)
+    reps, keep_rep = _reports(nboot, [p] * nboot, want_report)
     st = L.lingam_fit_bootstrap(ctypes.c_void_p(ptr), p, n, nboot, ctypes.c_void_p(iptr), order.ctypes.data,
                                 B.ctypes.data if B is not None else None, ctypes.c_void_p(workspace.data_ptr()),
-                                ctypes.byref(o), status.ctypes.data_as(_c_int_p), None)
+                                ctypes.byref(o), status.ctypes.data_as(_c_int_p), reps)
     del keep
-    return BatchResult(status=int(st), statuses=status, orders=list(order), Bs=list(B) if B is not None else None)
+    res = BatchResult(status=int(st), statuses=status, orders=list(order), Bs=list(B) if B is not None else None)
+    if keep_rep:
+        res.root_scores = [k[0] for k in keep_rep]
+        res.margins = [k[1] for k in keep_rep]
+        res.pairs = [k[2] for k in keep_rep]
+    return res
 
 
 STATIC_SCRATCH_BYTES = 32 << 20   # LINGAM_STATIC_SCRATCH_BYTES in include/lingam.h

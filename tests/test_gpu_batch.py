@@ -138,9 +138,14 @@ def test_bootstrap_matches_gathered_single_fits():
         o_order, o_B, o_S = oracle.fit(Xb)
         roots, margins = _oracle_margins(o_S)
         _agree_until_unresolved(res.orders[b], o_order, roots, margins)
-    # host indices and device indices give the same result
-    res2 = lingam.fit_bootstrap(_dev(X), torch.tensor(idx, device="cuda"), precision="mixed")
+    # host indices and device indices give the same result; reports carry every
+    # resample's evaluated pairs (at most all unordered pairs of each iteration)
+    res2 = lingam.fit_bootstrap(_dev(X), torch.tensor(idx, device="cuda"), precision="mixed", want_report=True)
     assert all(np.array_equal(a, b) for a, b in zip(res.orders, res2.orders))
+    assert len(res2.pairs) == 8
+    for pp in res2.pairs:
+        r = 20 - np.arange(20)
+        assert np.all(pp >= 0) and np.all(pp <= r * (r - 1) // 2) and pp[0] > 0
 
 
 def test_batch_degenerate_member_does_not_stop_the_others():
