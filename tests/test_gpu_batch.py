@@ -148,6 +148,25 @@ def test_bootstrap_matches_gathered_single_fits():
         assert np.all(pp >= 0) and np.all(pp <= r * (r - 1) // 2) and pp[0] > 0
 
 
+def test_batch_edge_sizes():
+    """Tiny and ragged members in one batch (p = 1, 2, 3 and tile-edge sizes, n down to 3):
+    every member succeeds and agrees with its single fit; p = 1 and 2 give the trivial
+    orders' structure (a permutation)."""
+    sizes = [(1, 50), (2, 3), (3, 5), (17, 257), (33, 1000), (65, 400), (2, 700)]
+    ds = [synth.lingam_dataset(p, n, min(1.0, 4.0 / max(p - 1, 1)), seed=90 + k).X.astype(np.float32)
+          for k, (p, n) in enumerate(sizes)]
+    Xs = [_dev(X) for X in ds]
+    res = lingam.fit_batch(Xs, precision="mixed")
+    assert res.status == 0 and np.all(res.statuses == 0)
+    for X, (p, n), o, B in zip(Xs, sizes, res.orders, res.Bs):
+        assert sorted(o.tolist()) == list(range(p))
+        single, roots, margins = _single(X)
+        k = _agree_until_unresolved(o, single.order, roots, margins)
+        print(f"p={p} n={n}: batch order equals the single fit on {k} of {p} iterations")
+        if k == p:
+            assert np.abs(B - single.B).max() <= 1e-6 * max(1.0, np.abs(single.B).max())
+
+
 def test_batch_degenerate_member_does_not_stop_the_others():
     ds = [synth.lingam_dataset(10, 800, 0.3, seed=70 + k).X.astype(np.float32) for k in range(3)]
     ds[1][4] = 2.5   # a constant row
