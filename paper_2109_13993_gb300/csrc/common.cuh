@@ -70,6 +70,13 @@ struct Ctl {
     // number within the iteration (bits 49-63), done (bit 48), tiles (32-47), columns
     // (24-31), rows (0-23); zero when the iteration is planned
     unsigned long long wave_word;
+    // written by the iteration's last wave finalisation for the removal and the next launch:
+    // U's size and the root of this iteration (the next iteration's plan, which may run
+    // during this removal, overwrites r and root), and the sequence number of the last
+    // published wave (wave words continue across the iterations of a fit)
+    int rm_r, rm_root;
+    unsigned seq0;
+    int pad3;
 };
 
 __host__ __device__ inline unsigned long long pack_wave(unsigned seq, int done, int ntiles, int ncol, int nrow) {
@@ -108,6 +115,8 @@ struct Fit {
     double* prev;        // [p] scores of the previous iteration (ordering of candidates)
     int* flags;          // [p]
     int* sigma;          // [p] alive variables in candidate order
+    int* sigma_alt;      // [p] the next iteration's candidate order (single fits: planned
+                         // during this iteration's removal; the host swaps the two per launch)
     int* rows;           // [p] rows of the current wave (variable ids)
     int* cols;           // [kTJ] columns of the current wave
     int* order;          // [p] causal order (device copy)

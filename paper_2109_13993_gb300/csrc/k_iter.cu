@@ -286,16 +286,16 @@ __device__ __forceinline__ int cta_of_unit(long long v, long long U, long long G
 
 // ------------------------------------------------------------------ plan (CTA 0)
 template <int NTH, int TI, int TJ>
-__device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* smem, int* red) {
+__device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* smem, int* red, int* sigma) {
     Ctl* ctl = f.ctl;
     const int p = f.p, tid = threadIdx.x;
     int r = 0;
     for (int base = 0; base < p; base += NTH) {   // U in index order
         const int v = base + tid;
-        const int a = (v < p) ? (f.flags[v] & kAlive) : 0;
+        const int a = (v < p) ? (ld2(f.flags + v) & kAlive) : 0;
         int tot;
         const int rank = r + scan01<NTH>(a ? 1 : 0, red, &tot);
-        if (a) f.sigma[rank] = v;
+        if (a) sigma[rank] = v;
         r += tot;
         __syncthreads();
     }
@@ -309,8 +309,8 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
         for (int k = tid; k < N; k += NTH) {
             unsigned long long kv = ~0ull;
             if (k < r) {
-                const int v = f.sigma[k];
-                const float sc = float(it == 0 ? f.hx[v] : f.prev[v]);
+                const int v = sigma[k];
+                const float sc = float(it == 0 ? ld2(f.hx + v) : ld2(f.prev + v));
                 unsigned int bits = __float_as_uint(sc);
                 bits = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
                 kv = (static_cast<unsigned long long>(bits) << 32) | static_cast<unsigned int>(v);
@@ -351,12 +351,12 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
                 }
             }
         }
-        for (int k = tid; k < r; k += NTH) f.sigma[k] = int(key[k] & 0xffffffffu);
+        for (int k = tid; k < r; k += NTH) sigma[k] = int(key[k] & 0xffffffffu);
         __syncthreads();
         fence_proxy_async();   // this shared memory is the copy ring of later phases
     }
     for (int k = tid; k < r; k += NTH) {
-        const int v = f.sigma[k];
+        const int v = sigma[k];
         f.part[v] = 0.0;
         f.flags[v] = kAlive;
         f.rows[k] = v;
@@ -372,10 +372,9 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
         ctl->best = INFINITY;
         ctl->best_var = -1;
         ctl->pairs_it = 0;
-        ctl->wave_word = 0;
         if (r <= 1) {
             // Algorithm 2: a single remaining variable is the root
-            const int root = r == 1 ? f.sigma[0] : -1;
+            const int root = r == 1 ? sigma[0] : -1;
             ctl->root = root;
             ctl->done = 1;
             if (root >= 0) {
@@ -389,7 +388,7 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
         } else {
             ctl->done = 0;
             const int nc = r < TJ ? r : TJ;
-            for (int c = 0; c < nc; ++c) f.cols[c] = f.sigma[c];
+            for (int c = 0; c < nc; ++c) f.cols[c] = sigma[c];
             ctl->ncol = nc;
             ctl->nrow = r;
             ctl->ntiles = (r + TI - 1) / TI;
@@ -640,6 +639,9 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
         const int ntiles_next = (nc + nr + TI - 1) / TI;
         if (nc == 0) {
             ctl->root = root;
+            ctl->rm_root = root;
+            ctl->rm_r = r;
+            if (seq != 0) ctl->seq0 = seq;
             ctl->done = 1;
             f.order[it] = root;
             f.rep_root_score[it] = root == bv ? best : ld2(f.part + root);
@@ -1144,7 +1146,7 @@ __device__ __noinline__ void remove_data_phase(const Fit& f, IterShared& sh, int
     using T = typename Cfg::T;
     constexpr int NTH = Cfg::CONS;
     volatile Ctl* vc = f.ctl;
-    const int r = vc->r, root = vc->root, p = f.p, ld = f.ld, tid = threadIdx.x;
+    const int r = vc->rm_r, root = vc->rm_root, p = f.p, ld = f.ld, tid = threadIdx.x;
     const int lane = tid & 31, wid = tid >> 5;
     const double* rootrow = f.sig + size_t(root) * p;
     const T* xr = static_cast<const T*>(f.xt) + size_t(root) * ld;
@@ -1213,7 +1215,7 @@ template <class Cfg>
 __device__ __noinline__ void remove_cov_phase(const Fit& f, int vb, int vG) {
     constexpr int NTH = Cfg::CONS;
     volatile Ctl* vc = f.ctl;
-    const int r = vc->r, root = vc->root, p = f.p, tid = threadIdx.x;
+    const int r = vc->rm_r, root = vc->rm_root, p = f.p, tid = threadIdx.x;
     const double* rootrow = f.sig + size_t(root) * p;
     const int nmine = r > vb ? (r - 1 - vb) / vG + 1 : 0;
     if (nmine == 0) return;
@@ -1258,6 +1260,24 @@ __device__ __noinline__ void remove_cov_phase(const Fit& f, int vb, int vG) {
 }
 
 // ------------------------------------------------------------------ the iteration kernel
+// The end of an iteration that took a root.  The grid's last CTA plans the next iteration
+// (its candidate order into f.sigma_alt, which the host passes as f.sigma to the next
+// launch): the plan needs the scores and U without the root, not the removal's results.
+// The other CTAs remove the root: UpdateData and UpdateCovMat touch disjoint memory (the
+// covariance's root column, from which the coefficients come, is not written) and none of
+// what the plan writes.  Out of line, so that the kernel around the pair waves stays small.
+template <class Cfg>
+__device__ __noinline__ void iteration_tail(const Fit& f, int it, IterShared& sh) {
+    if (*reinterpret_cast<volatile int*>(&f.ctl->rm_root) < 0) return;
+    const int fc = int(gridDim.x) - 1;
+    if (int(blockIdx.x) == fc) {
+        plan_phase<Cfg::CONS, Cfg::TI, Cfg::TJ>(f, it + 1, smem_dyn, sh.red, f.sigma_alt);
+    } else {
+        remove_data_phase<Cfg>(f, sh, int(blockIdx.x), gridDim.x - 1);
+        remove_cov_phase<Cfg>(f, int(blockIdx.x), gridDim.x - 1);
+    }
+}
+
 // Wait (bounded) until the wave finalisation of a single fit has published wave word
 // seq; returns the next wave and whether the iteration is done.  Returns false when
 // this CTA gave up (timeout, recorded) or another CTA did.
@@ -1327,8 +1347,12 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
     }
     __syncthreads();
 
-    if (blockIdx.x == 0) plan_phase<Cfg::CONS, Cfg::TI, Cfg::TJ>(f, it, smem_raw, sh.red);
-    if (!grid_sync(ctl, tmo)) return;
+    // Iteration 0 is planned here; every later one was planned by the previous launch, during
+    // its removal (the candidate order in f.sigma, the first wave in the control block).
+    if (it == 0) {
+        if (blockIdx.x == 0) plan_phase<Cfg::CONS, Cfg::TI, Cfg::TJ>(f, it, smem_raw, sh.red, f.sigma);
+        if (!grid_sync(ctl, tmo)) return;
+    }
     int chunk_base = 0;
     // phase times (opts.timing): CTA 0's global timer at the phase boundaries, which follow
     // grid barriers, so each interval covers the slowest CTA of the phase
@@ -1337,7 +1361,8 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
     // the first wave as planned; later ones as published by each wave's finalisation
     Wave wv = {vc->ntiles, vc->ncol, vc->nrow};
     bool done = vc->done != 0;
-    for (unsigned seq = 1; !done; ++seq) {
+    // wave words are numbered on from the last wave of the previous iteration
+    for (unsigned seq = *reinterpret_cast<volatile unsigned*>(&ctl->seq0) + 1; !done; ++seq) {
         const Span sp = single_span((long long)wv.ntiles * (f.ld / kSub), gridDim.x);
         if (!compute_phase<Cfg>(f, ctl, wv, sp, ring, full, empty, sh, chunk_base)) {
             ctl->abort = 1;
@@ -1360,11 +1385,8 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
             tph = t;
         }
     }
-    if (it < f.p - 1 && vc->root >= 0) {
-        // UpdateData and UpdateCovMat touch disjoint memory (the covariance's root column,
-        // from which the data coefficients come, is not written): no barrier between them
-        remove_data_phase<Cfg>(f, sh, blockIdx.x, gridDim.x);
-        remove_cov_phase<Cfg>(f, blockIdx.x, gridDim.x);
+    if (it < f.p - 1) {
+        iteration_tail<Cfg>(f, it, sh);
         if (timed) ctl->phase_ns[2] += global_ns() - tph;
     }
 }
@@ -1768,7 +1790,7 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
         // plan (a problem whose status turned bad stays done: it is not planned again)
         batch_active(fits, count, it, 0, bs);
         for (int d = blockIdx.x; d < count; d += gridDim.x)
-            if (bs.act[d]) plan_phase<CONS, TI, Cfg::TJ>(fits[d], it, smem_raw, sh.red);
+            if (bs.act[d]) plan_phase<CONS, TI, Cfg::TJ>(fits[d], it, smem_raw, sh.red, fits[d].sigma);
         if (!grid_sync(bctl, tmo)) return;
         for (;;) {
             long long utot;

@@ -41,7 +41,7 @@ static size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
     size_t total = 0;
-    size_t off_xin, off_xt, off_mu, off_sd, off_sig, off_sig0, off_hx, off_part, off_prev, off_flags, off_sigma,
+    size_t off_xin, off_xt, off_mu, off_sd, off_sig, off_sig0, off_hx, off_part, off_prev, off_flags, off_sigma, off_sigma_alt,
         off_rows, off_cols, off_order, off_forced, off_scratch, off_rowsum, off_colsum, off_partials, off_invroot,
         off_tilecnt, off_rs, off_rm, off_rp, off_rsc, off_cmat, off_rmat, off_rinv, off_bout, off_ctl, off_ibuf;
     int ld, maxtiles, maxsplit, esz;
@@ -78,6 +78,7 @@ static Layout make_layout(long long p, long long n, int precision, int input_dty
     L.off_prev = take(P * 8);
     L.off_flags = take(P * 4);
     L.off_sigma = take(P * 4);
+    L.off_sigma_alt = take(P * 4);
     L.off_rows = take((P + kTJ) * 4);   // the finalisation may write up to kTJ past the rows
     L.off_cols = take(kTJ * 4);
     L.off_order = take(P * 4);
@@ -151,6 +152,7 @@ static Fit make_fit(char* base, const Layout& L, int p, int n, const lingam_opts
     f.prev = reinterpret_cast<double*>(base + L.off_prev);
     f.flags = reinterpret_cast<int*>(base + L.off_flags);
     f.sigma = reinterpret_cast<int*>(base + L.off_sigma);
+    f.sigma_alt = reinterpret_cast<int*>(base + L.off_sigma_alt);
     f.rows = reinterpret_cast<int*>(base + L.off_rows);
     f.cols = reinterpret_cast<int*>(base + L.off_cols);
     f.order = reinterpret_cast<int*>(base + L.off_order);
@@ -278,7 +280,11 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
                 pev.push_back(e1);
                 cudaEventRecord(e0, st);
             }
-            if (launch_iteration(f, it, grid, st) != cudaSuccess) status = LINGAM_ECUDA;
+            // the candidate orders alternate between the two lists: iteration it reads the
+            // one the previous launch planned and plans the next into the other
+            Fit fi = f;
+            if (it & 1) std::swap(fi.sigma, fi.sigma_alt);
+            if (launch_iteration(fi, it, grid, st) != cudaSuccess) status = LINGAM_ECUDA;
             ++launches;
             if (o.timing) cudaEventRecord(e1, st);
         }
