@@ -38,7 +38,7 @@ SFU_CLK_PER_PAIR_SAMPLE = 4.0 / 32.0 + (2.0 / 32.0) / 16.0
 # of iterations 2 and 3 of a p = 1000, n = 1e4 fit (cold caches: the 40 MB of
 # normalised rows and the 8 MB covariance read once).  Valid for this kernel
 # version only: set to None when the kernel changes, until it is captured again.
-ITER_TRAFFIC_BYTES = None
+ITER_TRAFFIC_BYTES = 48.60e6 + 7.60e6
 
 
 def unpruned_pair_samples(p: int, n: int) -> float:

@@ -5,9 +5,12 @@
 // grid barriers instead of kernel launches.
 //
 // Phases of an iteration:
-//   plan     (CTA 0) candidate order sigma of the remaining variables U, sorted
-//            by the previous iteration's scores (iteration 0: H(x) - H(nu), most
+//   plan     candidate order sigma of the remaining variables U, sorted by the
+//            previous iteration's scores (iteration 0: H(x) - H(nu), most
 //            non-Gaussian first); the first wave's columns are its first TJ.
+//            Iteration 0 is planned by CTA 0 at the start of its launch; every
+//            later iteration by the grid's last CTA during the previous
+//            iteration's removal (into the second candidate list).
 //   waves    repeat until no live candidate is left:
 //     compute  every CTA evaluates its share of the wave's (tile, chunk) units
 //              and writes partial sample moments;
@@ -16,7 +19,7 @@
 //              per-column score contributions; the CTA that merges the wave's
 //              last tile runs the wave finalisation (scores, threshold, prune,
 //              next wave or root).
-//   remove   rows of U spread over the CTAs: x_w <- (x_w - Sigma[w,root] x_root)
+//   remove   rows of U spread over the other CTAs: x_w <- (x_w - Sigma[w,root] x_root)
 //            / sqrt(1 - Sigma[w,root]^2) with the new H(x_w); then the covariance
 //            downdate of Eq. CovUpdate, in FP64.
 //
