@@ -96,8 +96,9 @@ typedef struct {
     long long pairs_unpruned;    /* sum over iterations of r(r-1)/2 (r(r-1) when reuse = 0) */
     double t_pair_ms;            /* device time of the pair-comparison launches (opts.timing = 1), else 0 */
     long long kernel_launches;   /* kernels this call launched */
-    double* t_pair_iter_ms;      /* NULL or a HOST array [p]: with opts.timing = 1, device time of the
-                                    pair comparison of iteration k (iterations with r >= 2) */
+    double* t_pair_iter_ms;      /* NULL or a HOST array [p]: with opts.timing = 1, the time of the
+                                    launch of iteration k, between the stream events recorded after
+                                    launch k - 1 (before the first launch) and after launch k */
     /* With opts.timing = 1 (single fits): device wall time (global timer, summed over all
        iterations) of the pair-compute phases of the waves, of their merge and finalisation
        phases, and of the removals (UpdateData, UpdateCovMat); each interval ends at a grid

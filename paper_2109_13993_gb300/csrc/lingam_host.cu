@@ -269,16 +269,25 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
             status = LINGAM_ECUDA;
             break;
         }
+        // opts.timing: one event before the first launch and one after each, so launch it
+        // is timed between events it and it + 1 (consecutive launches share an event)
+        if (o.timing) {
+            cudaEvent_t e0 = nullptr;
+            if (cudaEventCreate(&e0) != cudaSuccess) {
+                status = LINGAM_ECUDA;
+                break;
+            }
+            pev.push_back(e0);
+            cudaEventRecord(e0, st);
+        }
         for (int it = 0; it < iters && status == LINGAM_OK; ++it) {
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            cudaEvent_t e1 = nullptr;
             if (o.timing) {
-                if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+                if (cudaEventCreate(&e1) != cudaSuccess) {
                     status = LINGAM_ECUDA;
                     break;
                 }
-                pev.push_back(e0);
                 pev.push_back(e1);
-                cudaEventRecord(e0, st);
             }
             // the candidate orders alternate between the two lists: iteration it reads the
             // one the previous launch planned and plans the next into the other
@@ -325,10 +334,10 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
             rep->t_order_ms = cudaEventElapsedTime(&ms, ev[2], ev[3]) == cudaSuccess ? ms : -1.0;
             rep->t_B_ms = (want_B && cudaEventElapsedTime(&ms, ev[3], ev[4]) == cudaSuccess) ? ms : 0.0;
             double tp = 0.0;
-            for (size_t k = 0; k + 1 < pev.size(); k += 2)
+            for (size_t k = 0; k + 1 < pev.size(); ++k)
                 if (cudaEventElapsedTime(&ms, pev[k], pev[k + 1]) == cudaSuccess) {
                     tp += ms;
-                    if (rep->t_pair_iter_ms && k / 2 < size_t(p)) rep->t_pair_iter_ms[k / 2] = ms;
+                    if (rep->t_pair_iter_ms && k < size_t(p)) rep->t_pair_iter_ms[k] = ms;
                 }
             rep->t_pair_ms = tp;
             rep->kernel_launches = launches;
