@@ -7,6 +7,8 @@
 // triangular), the innovations e = diag(R) R^{-1} x are uncorrelated and
 // x = (I - diag(R) R^{-1}) x + e, so B_K = I - diag(R) R^{-1}, strictly lower
 // triangular; B is B_K with rows and columns mapped back to variable indices.
+#include <algorithm>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -21,23 +23,64 @@ __global__ void k_perm_cov(Fit f) {
     f.cmat[size_t(a) * p + b] = f.sd[ia] * f.sd[ib] * f.sig0[size_t(ia) * p + ib];
 }
 
-// Right-looking Cholesky, step k: column k of R (stored as row k of Rt = rmat)
-// and the Schur-complement update of the trailing lower triangle.
-__global__ void k_chol_step(Fit f, int k) {
-    const int p = f.p;
-    const double ckk = f.cmat[size_t(k) * p + k];
-    if (!(ckk > 0.0)) {
-        if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) set_status(f.ctl, LINGAM_EDEGENERATE);
-        return;
+// Right-looking Cholesky C = R R^T (R lower) in one cooperative launch, one grid barrier
+// per column.  The working matrix is the upper triangle U of C (row k of U holds column
+// k of C, so every access below is along a row): at step k, row k of rmat receives
+// R[i][k] = U[k][i] / sqrt(U[k][k]) (i >= k), and the rows i > k of the trailing
+// triangle lose the rank-one term: U[i][j] -= U[k][i] U[k][j] / U[k][k] (j >= i).  A
+// non-positive pivot records LINGAM_EDEGENERATE (every CTA reads the same pivot, so all
+// leave together); the barrier's waits are bounded by the fit's timeout.
+__device__ bool bfit_grid_sync(Ctl* ctl) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned G = gridDim.x;
+        __threadfence();
+        const unsigned old = atomicAdd(&ctl->bfit_bar, 1u);
+        const unsigned target = old - old % G + G;
+        volatile unsigned* cntp = &ctl->bfit_bar;
+        const unsigned long long tmo = *reinterpret_cast<volatile unsigned long long*>(&ctl->timeout_ns);
+        unsigned long long t0 = 0;
+        while (int(*cntp - target) < 0) {
+            const unsigned long long now = global_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > tmo) {
+                set_status(ctl, LINGAM_ETIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        s_ok = ok;
     }
-    if (blockIdx.x == 0 && blockIdx.y == 0) {
-        const double rk = sqrt(ckk);
-        for (int i = k + threadIdx.x; i < p; i += blockDim.x) f.rmat[size_t(k) * p + i] = f.cmat[size_t(i) * p + k] / rk;
+    __syncthreads();
+    return s_ok != 0;
+}
+
+constexpr int kCholThreads = 256;
+
+__global__ void __launch_bounds__(kCholThreads) k_chol_coop(Fit f) {
+    const int p = f.p, tid = threadIdx.x;
+    double* U = f.cmat;
+    for (int k = 0; k < p; ++k) {
+        const double* uk = U + size_t(k) * p;
+        const double ukk = __ldcg(uk + k);
+        if (!(ukk > 0.0)) {
+            if (threadIdx.x == 0 && blockIdx.x == 0) set_status(f.ctl, LINGAM_EDEGENERATE);
+            return;
+        }
+        const double rk = sqrt(ukk), inv = 1.0 / ukk;
+        if (blockIdx.x == gridDim.x - 1)
+            for (int i = k + tid; i < p; i += kCholThreads) f.rmat[size_t(k) * p + i] = __ldcg(uk + i) / rk;
+        for (int i = k + 1 + int(blockIdx.x); i < p; i += gridDim.x) {
+            const double a = __ldcg(uk + i) * inv;
+            double* ui = U + size_t(i) * p;
+            for (int j = i + tid; j < p; j += kCholThreads) ui[j] = fma(-a, __ldcg(uk + j), __ldcg(ui + j));
+        }
+        if (!bfit_grid_sync(f.ctl)) return;
     }
-    const int i = k + 1 + blockIdx.y * 16 + (threadIdx.x >> 4);
-    const int j = k + 1 + blockIdx.x * 16 + (threadIdx.x & 15);
-    if (i >= p || j > i) return;
-    f.cmat[size_t(i) * p + j] -= f.cmat[size_t(i) * p + k] * f.cmat[size_t(j) * p + k] / ckk;
 }
 
 // Column j of R^{-1} by forward substitution (one CTA per column):
@@ -141,13 +184,29 @@ cudaError_t launch_fit_B(const Fit& f, cudaStream_t st) {
     const int p = f.p;
     dim3 g2((p + 15) / 16, (p + 15) / 16);
     k_perm_cov<<<g2, 256, 0, st>>>(f);
-    for (int k = 0; k < p; ++k) {
-        const int m = p - k - 1;
-        dim3 g(m > 0 ? (m + 15) / 16 : 1, m > 0 ? (m + 15) / 16 : 1);
-        k_chol_step<<<g, 256, 0, st>>>(f, k);
-    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, kCholThreads, 0)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    {
+        // one CTA per SM at most (co-resident: cooperative launch), no more than rows
+        const int grid = std::max(1, std::min(nsm, p));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kCholThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if ((e = cudaLaunchKernelEx(&cfg, k_chol_coop, f)) != cudaSuccess) return e;
+    }
     const size_t smem = size_t(p) * sizeof(double);
     e = ensure_smem_attr(reinterpret_cast<const void*>(k_tri_inv), smem);
     if (e != cudaSuccess) return e;

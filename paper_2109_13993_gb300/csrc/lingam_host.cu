@@ -300,7 +300,7 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
         if (status != LINGAM_OK) break;
         if (cudaEventRecord(ev[3], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
         if (want_B && launch_fit_B(f, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
-        if (want_B) launches += 3 + p;
+        if (want_B) launches += 4;
         if (cudaEventRecord(ev[4], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
     } while (0);
     if (cudaStreamSynchronize(st) != cudaSuccess) status = LINGAM_ECUDA;
