@@ -61,8 +61,13 @@ __device__ bool bfit_grid_sync(Ctl* ctl) {
 
 constexpr int kCholThreads = 256;
 
+constexpr int kCholRows = 128;   // rows of one CTA staged at a time
+constexpr int kCholBatch = 8;    // elements per thread with their loads in flight together
+
 __global__ void __launch_bounds__(kCholThreads) k_chol_coop(Fit f) {
-    const int p = f.p, tid = threadIdx.x;
+    __shared__ int s_i[kCholRows], s_off[kCholRows + 1];
+    __shared__ double s_a[kCholRows];
+    const int p = f.p, tid = threadIdx.x, b = blockIdx.x, G = gridDim.x;
     double* U = f.cmat;
     for (int k = 0; k < p; ++k) {
         const double* uk = U + size_t(k) * p;
@@ -72,12 +77,59 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_coop(Fit f) {
             return;
         }
         const double rk = sqrt(ukk), inv = 1.0 / ukk;
-        if (blockIdx.x == gridDim.x - 1)
+        if (b == G - 1)
             for (int i = k + tid; i < p; i += kCholThreads) f.rmat[size_t(k) * p + i] = __ldcg(uk + i) / rk;
-        for (int i = k + 1 + int(blockIdx.x); i < p; i += gridDim.x) {
-            const double a = __ldcg(uk + i) * inv;
-            double* ui = U + size_t(i) * p;
-            for (int j = i + tid; j < p; j += kCholThreads) ui[j] = fma(-a, __ldcg(uk + j), __ldcg(ui + j));
+        // this CTA's rows i = k + 1 + b, + G, ...: their elements (i, j >= i) numbered one
+        // after another, so that each thread has several independent updates in flight
+        for (int i0 = k + 1 + b; i0 < p; i0 += kCholRows * G) {
+            __syncthreads();   // the previous block's row table is no longer read
+            const int nr = min(kCholRows, (p - 1 - i0) / G + 1);
+            for (int r = tid; r < nr; r += kCholThreads) {
+                const int i = i0 + r * G;
+                s_i[r] = i;
+                s_a[r] = __ldcg(uk + i) * inv;
+            }
+            if (tid == 0) {
+                int o = 0;
+                for (int r = 0; r < nr; ++r) {
+                    s_off[r] = o;
+                    o += p - (i0 + r * G);
+                }
+                s_off[nr] = o;
+            }
+            __syncthreads();
+            const int tot = s_off[nr];
+            for (int base = tid; base < tot; base += kCholBatch * kCholThreads) {
+                size_t at[kCholBatch];
+                int jj[kCholBatch];
+                double av[kCholBatch], x[kCholBatch], y[kCholBatch];
+#pragma unroll
+                for (int q = 0; q < kCholBatch; ++q) {
+                    const int idx = base + q * kCholThreads;
+                    jj[q] = -1;
+                    if (idx < tot) {
+                        int lo = 0, hi = nr - 1;   // the row: last r with s_off[r] <= idx
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (s_off[mid] <= idx) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        const int i = s_i[lo];
+                        jj[q] = i + (idx - s_off[lo]);
+                        at[q] = size_t(i) * p + jj[q];
+                        av[q] = s_a[lo];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kCholBatch; ++q)
+                    if (jj[q] >= 0) {
+                        x[q] = __ldcg(uk + jj[q]);
+                        y[q] = __ldcg(U + at[q]);
+                    }
+#pragma unroll
+                for (int q = 0; q < kCholBatch; ++q)
+                    if (jj[q] >= 0) U[at[q]] = fma(-av[q], x[q], y[q]);
+            }
         }
         if (!bfit_grid_sync(f.ctl)) return;
     }
