@@ -52,8 +52,10 @@
 // partial slot per tile it touches (slot index tile + b is unique).  Inside a
 // CTA the sample chunks of the TI + 32 variables of the current tile stream
 // into a shared-memory ring with 1-D bulk copies (TMA engine) completing on
-// mbarriers; the warp that releases a stage last refills it.  Every wait
-// (mbarrier phase, grid barrier) is bounded by the fit's timeout.
+// "full" mbarriers; each warp releases a stage on its "empty" mbarrier and,
+// once every warp has released it, copies its own rows of a later chunk into it.
+// Every wait (mbarrier phase, grid barrier, wave word) is bounded by the fit's
+// timeout.
 #include <type_traits>
 
 #include "common.cuh"
