@@ -998,14 +998,14 @@ __device__ __forceinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wav
 }
 
 // ------------------------------------------------------------------ merge phase
-// A tile's partial slots are merged in kMergeParts items, one per group of 64
+// A tile's partial slots are merged in CONS / 64 items, one per group of 64
 // compute threads (256 pairs, 1024 values per slot), spread over the CTAs.  In an
 // item each warp sums the slots w, w + NW, ... in order, then the warps' sums are
 // added in warp order: a fixed summation order, independent of timing.  The item
-// evaluates I (Eq. Itest with Eq. HApp) for its 256 pairs and stores them in the
-// tile's I buffer; the item that completes a tile reduces its rows and columns
-// (squared contributions summed in FP64), and the item that completes the wave's
-// last tile runs the wave finalisation.
+// evaluates I (Eq. Itest with Eq. HApp) for its 256 pairs, which make complete
+// rows of the tile: it writes those rows' contributions min(0, I)^2 over all
+// columns and its part of each column's max(0, I)^2 (float-float sums, FP64
+// results), and the item that completes the wave runs the wave finalisation.
 template <class Cfg>
 __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span& sp, int it, IterShared& sh,
                                         typename Cfg::T* scratch, int item, unsigned seq) {
