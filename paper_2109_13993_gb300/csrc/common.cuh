@@ -62,7 +62,7 @@ struct Ctl {
     long long pairs_it;  // pairs evaluated this iteration
     unsigned long long timeout_ns;  // bound on device-side waits
     unsigned bar_count;  // grid barrier: arrivals since the fit started (never reset)
-    unsigned bfit_bar;   // grid barrier of the B fit's Cholesky (its own count, from 0)
+    int pad0;
     int abort;           // set when a CTA gives up a wait; the others then leave too
     int pad1;
     unsigned long long phase_ns[3];   // with timing: pair compute, merge + finalise, removal (CTA 0)

@@ -23,115 +23,130 @@ __global__ void k_perm_cov(Fit f) {
     f.cmat[size_t(a) * p + b] = f.sd[ia] * f.sd[ib] * f.sig0[size_t(ia) * p + ib];
 }
 
-// Right-looking Cholesky C = R R^T (R lower) in one cooperative launch, one grid barrier
-// per column.  The working matrix is the upper triangle U of C (row k of U holds column
-// k of C, so every access below is along a row): at step k, row k of rmat receives
-// R[i][k] = U[k][i] / sqrt(U[k][k]) (i >= k), and the rows i > k of the trailing
-// triangle lose the rank-one term: U[i][j] -= U[k][i] U[k][j] / U[k][k] (j >= i).  A
-// non-positive pivot records LINGAM_EDEGENERATE (every CTA reads the same pivot, so all
-// leave together); the barrier's waits are bounded by the fit's timeout.
-__device__ bool bfit_grid_sync(Ctl* ctl) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned G = gridDim.x;
-        __threadfence();
-        const unsigned old = atomicAdd(&ctl->bfit_bar, 1u);
-        const unsigned target = old - old % G + G;
-        volatile unsigned* cntp = &ctl->bfit_bar;
-        const unsigned long long tmo = *reinterpret_cast<volatile unsigned long long*>(&ctl->timeout_ns);
-        unsigned long long t0 = 0;
-        while (int(*cntp - target) < 0) {
-            const unsigned long long now = global_ns();
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > tmo) {
-                set_status(ctl, LINGAM_ETIMEOUT);
-                ok = 0;
-                break;
-            }
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
+// Right-looking Cholesky C = R R^T (R lower) in one cooperative launch, as a data flow
+// over rows.  The working matrix is the upper triangle U of C (row k of U holds column k
+// of C, so every access below is along a row).  At step k, row k of rmat receives
+// R[i][k] = U[k][i] / sqrt(U[k][k]) (i >= k) and the rows i > k lose the rank-one term
+// U[i][j] -= U[k][i] U[k][j] / U[k][k] (j >= i).  Row i belongs to CTA i mod G for the
+// whole factorisation, so its successive updates follow one another inside one CTA;
+// step k needs only row k final, which its owner publishes (ready[k] = 1) as soon as
+// it has applied step k - 1 to it, before its other rows, so the next steps start while
+// the bulk of the current one is still running.  A non-positive pivot records
+// LINGAM_EDEGENERATE (every CTA reads the same final pivot, so all leave at the same
+// step); every wait is bounded by the fit's timeout.
 constexpr int kCholThreads = 256;
-
 constexpr int kCholRows = 128;   // rows of one CTA staged at a time
 constexpr int kCholBatch = 8;    // elements per thread with their loads in flight together
+
+// U[i][j] -= a U[k][j] for the rows i0, i0 + G, ... (< p, at most kCholRows of them) and
+// j >= i, their elements numbered one after another over the CTA's threads.
+__device__ void chol_rows(double* U, const double* uk, double inv, int p, int i0, int G, int* s_i, int* s_off,
+                          double* s_a) {
+    const int tid = threadIdx.x;
+    const int nr = min(kCholRows, (p - 1 - i0) / G + 1);
+    __syncthreads();   // the previous row table is no longer read
+    for (int r = tid; r < nr; r += kCholThreads) {
+        const int i = i0 + r * G;
+        s_i[r] = i;
+        s_a[r] = __ldcg(uk + i) * inv;
+    }
+    if (tid == 0) {
+        int o = 0;
+        for (int r = 0; r < nr; ++r) {
+            s_off[r] = o;
+            o += p - (i0 + r * G);
+        }
+        s_off[nr] = o;
+    }
+    __syncthreads();
+    const int tot = s_off[nr];
+    for (int base = tid; base < tot; base += kCholBatch * kCholThreads) {
+        size_t at[kCholBatch];
+        int jj[kCholBatch];
+        double av[kCholBatch], x[kCholBatch], y[kCholBatch];
+#pragma unroll
+        for (int q = 0; q < kCholBatch; ++q) {
+            const int idx = base + q * kCholThreads;
+            jj[q] = -1;
+            if (idx < tot) {
+                int lo = 0, hi = nr - 1;   // the row: last r with s_off[r] <= idx
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= idx) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int i = s_i[lo];
+                jj[q] = i + (idx - s_off[lo]);
+                at[q] = size_t(i) * p + jj[q];
+                av[q] = s_a[lo];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kCholBatch; ++q)
+            if (jj[q] >= 0) {
+                x[q] = __ldcg(uk + jj[q]);
+                y[q] = __ldcg(U + at[q]);
+            }
+#pragma unroll
+        for (int q = 0; q < kCholBatch; ++q)
+            if (jj[q] >= 0) U[at[q]] = fma(-av[q], x[q], y[q]);
+    }
+}
 
 __global__ void __launch_bounds__(kCholThreads) k_chol_coop(Fit f) {
     __shared__ int s_i[kCholRows], s_off[kCholRows + 1];
     __shared__ double s_a[kCholRows];
+    __shared__ int s_ok;
     const int p = f.p, tid = threadIdx.x, b = blockIdx.x, G = gridDim.x;
     double* U = f.cmat;
+    int* ready = f.scratch;   // ready[k] = 1: row k final (zeroed by the host)
     for (int k = 0; k < p; ++k) {
+        if (tid == 0) {
+            int ok = 1;
+            if (k > 0) {
+                volatile int* rk_flag = ready + k;
+                unsigned long long t0 = 0, tmo = 0;
+                while (*rk_flag == 0) {
+                    const unsigned long long now = global_ns();
+                    if (t0 == 0) {
+                        t0 = now;
+                        tmo = *reinterpret_cast<volatile unsigned long long*>(&f.ctl->timeout_ns);
+                    } else if (now - t0 > tmo) {
+                        set_status(f.ctl, LINGAM_ETIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+                __threadfence();
+            }
+            s_ok = ok;
+        }
+        __syncthreads();   // also orders this CTA's writes of step k - 1 before its reads
+        if (!s_ok) return;
         const double* uk = U + size_t(k) * p;
         const double ukk = __ldcg(uk + k);
         if (!(ukk > 0.0)) {
-            if (threadIdx.x == 0 && blockIdx.x == 0) set_status(f.ctl, LINGAM_EDEGENERATE);
+            if (tid == 0 && b == k % G) set_status(f.ctl, LINGAM_EDEGENERATE);
             return;
         }
-        const double rk = sqrt(ukk), inv = 1.0 / ukk;
-        if (b == G - 1)
-            for (int i = k + tid; i < p; i += kCholThreads) f.rmat[size_t(k) * p + i] = __ldcg(uk + i) / rk;
-        // this CTA's rows i = k + 1 + b, + G, ...: their elements (i, j >= i) numbered one
-        // after another, so that each thread has several independent updates in flight
-        for (int i0 = k + 1 + b; i0 < p; i0 += kCholRows * G) {
-            __syncthreads();   // the previous block's row table is no longer read
-            const int nr = min(kCholRows, (p - 1 - i0) / G + 1);
-            for (int r = tid; r < nr; r += kCholThreads) {
-                const int i = i0 + r * G;
-                s_i[r] = i;
-                s_a[r] = __ldcg(uk + i) * inv;
-            }
-            if (tid == 0) {
-                int o = 0;
-                for (int r = 0; r < nr; ++r) {
-                    s_off[r] = o;
-                    o += p - (i0 + r * G);
-                }
-                s_off[nr] = o;
-            }
+        const double inv = 1.0 / ukk;
+        // row k + 1 first, published as soon as it is final
+        const int i1 = k + 1;
+        if (i1 < p && i1 % G == b) {
+            chol_rows(U, uk, inv, p, i1, p, s_i, s_off, s_a);   // stride p: this row alone
             __syncthreads();
-            const int tot = s_off[nr];
-            for (int base = tid; base < tot; base += kCholBatch * kCholThreads) {
-                size_t at[kCholBatch];
-                int jj[kCholBatch];
-                double av[kCholBatch], x[kCholBatch], y[kCholBatch];
-#pragma unroll
-                for (int q = 0; q < kCholBatch; ++q) {
-                    const int idx = base + q * kCholThreads;
-                    jj[q] = -1;
-                    if (idx < tot) {
-                        int lo = 0, hi = nr - 1;   // the row: last r with s_off[r] <= idx
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (s_off[mid] <= idx) lo = mid;
-                            else hi = mid - 1;
-                        }
-                        const int i = s_i[lo];
-                        jj[q] = i + (idx - s_off[lo]);
-                        at[q] = size_t(i) * p + jj[q];
-                        av[q] = s_a[lo];
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < kCholBatch; ++q)
-                    if (jj[q] >= 0) {
-                        x[q] = __ldcg(uk + jj[q]);
-                        y[q] = __ldcg(U + at[q]);
-                    }
-#pragma unroll
-                for (int q = 0; q < kCholBatch; ++q)
-                    if (jj[q] >= 0) U[at[q]] = fma(-av[q], x[q], y[q]);
+            if (tid == 0) {
+                __threadfence();
+                atomicExch(ready + i1, 1);
             }
         }
-        if (!bfit_grid_sync(f.ctl)) return;
+        if (b == k % G) {
+            const double rk = sqrt(ukk);
+            for (int i = k + tid; i < p; i += kCholThreads) f.rmat[size_t(k) * p + i] = __ldcg(uk + i) / rk;
+        }
+        // this CTA's other rows i > k + 1 (i = b mod G), in blocks of kCholRows
+        const int ifirst = k + 2 + ((b - (k + 2)) % G + G) % G;
+        for (int i0 = ifirst; i0 < p; i0 += kCholRows * G) chol_rows(U, uk, inv, p, i0, G, s_i, s_off, s_a);
     }
 }
 
@@ -244,6 +259,7 @@ cudaError_t launch_fit_B(const Fit& f, cudaStream_t st) {
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, kCholThreads, 0)) != cudaSuccess)
         return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if ((e = cudaMemsetAsync(f.scratch, 0, size_t(p) * sizeof(int), st)) != cudaSuccess) return e;   // row flags
     {
         // one CTA per SM at most (co-resident: cooperative launch), no more than rows
         const int grid = std::max(1, std::min(nsm, p));
