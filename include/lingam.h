@@ -99,10 +99,11 @@ typedef struct {
     double* t_pair_iter_ms;      /* NULL or a HOST array [p]: with opts.timing = 1, the time of the
                                     launch of iteration k, between the stream events recorded after
                                     launch k - 1 (before the first launch) and after launch k */
-    /* With opts.timing = 1 (single fits): device wall time (global timer, summed over all
-       iterations) of the pair-compute phases of the waves, of their merge and finalisation
-       phases, and of the removals (UpdateData, UpdateCovMat); each interval ends at a grid
-       barrier, so it covers the slowest CTA.  0 otherwise. */
+    /* With opts.timing = 1 (single fits): device wall time (CTA 0's global timer, summed
+       over all iterations) of the pair-compute phases of the waves (each ends at a grid
+       barrier, so it covers the slowest CTA), of their merge and finalisation phases (each
+       ends when CTA 0 sees the wave's published result), and of the removals (UpdateData,
+       UpdateCovMat; with the next iteration's planning when CTA 0 does it).  0 otherwise. */
     double t_compute_ms, t_merge_ms, t_remove_ms;
 } lingam_report;
 
