@@ -102,8 +102,8 @@ typedef struct {
     /* With opts.timing = 1 (single fits): device wall time (CTA 0's global timer, summed
        over all iterations) of the pair-compute phases of the waves (each ends at a grid
        barrier, so it covers the slowest CTA), of their merge and finalisation phases (each
-       ends when CTA 0 sees the wave's published result), and of the removals (UpdateData,
-       UpdateCovMat; with the next iteration's planning when CTA 0 does it).  0 otherwise. */
+       ends when CTA 0 sees the wave's published result), and of CTA 0's part of the
+       removals (UpdateData, UpdateCovMat).  0 otherwise. */
     double t_compute_ms, t_merge_ms, t_remove_ms;
 } lingam_report;
 
