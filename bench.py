@@ -30,6 +30,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 P_DEFAULT, N_DEFAULT = 1000, 10000
+# One metric and workload description for both arms (the reference arm is the FP64 CPU
+# oracle on the same data).
+METRIC = "pair-sample evals/s (unpruned-equivalent) at p=1000, n=1e4"
+
+
+def workload_name(p: int, n: int) -> str:
+    return f"p{p}_n{n} LiNGAM, expected in-degree 2, FP32-representable data, seed = rank+1"
+
+
 L2_FLUSH_BYTES = 256 << 20
 # Pair kernel SFU roofline: per pair-sample 4 ex2 (32 per SM per clock on sm_103a)
 # plus 2 lg2 per 32 samples (16 per SM per clock).
@@ -168,11 +177,12 @@ def run_reference(args, rank: int, world: int):
     value = float(np.mean(rates))
     sample = (f"oracle FindRoot (Algorithm 2, every ordered pair) over {int(np.mean(ms))} of the 1000 variables "
               f"of the p=1000, n=10000 dataset per step; rate in unpruned-equivalent pair-samples")
-    line = {"impl": "reference", "metric": "pair-sample evals/s (unpruned-equivalent) at p=1000, n=1e4",
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "pair-samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "p1000_n10000 LiNGAM, expected in-degree 2, seed 1", "p": 1000, "n": 10000},
+            "config": {"workload": workload_name(P_DEFAULT, N_DEFAULT), "p": P_DEFAULT, "n": N_DEFAULT,
+                       "arm": "FP64 CPU oracle, every ordered pair (no pruning)"},
             "cpu_baseline": {"value": value, "unit": "pair-samples/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "pair-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -348,11 +358,12 @@ def run_ours(args, rank: int, world: int):
     roofline["compute_phase"] = {"achieved": comp / 1e9, "frac": comp / peak,
                                  "ms_per_step": {"pair_compute": ph[0], "merge_finalize": ph[1], "removal": ph[2]}}
 
-    line = {"metric": "pair-sample evals/s (unpruned-equivalent) at p=1000, n=1e4, mixed path",
+    line = {"metric": METRIC if (p, n) == (P_DEFAULT, N_DEFAULT) else
+            f"pair-sample evals/s (unpruned-equivalent) at p={p}, n={n}",
             "value": value, "unit": "pair-samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"p{p}_n{n} LiNGAM, expected in-degree 2, FP32 storage, seed = rank+1",
+            "config": {"workload": workload_name(p, n),
                        "p": p, "n": n, "precision": "mixed", "prune": True, "reuse": True,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"independent datasets x{world}"},
             "ordering_ms": ms_per_step, "pairs_evaluated_per_step": int(np.mean(pairs)),
