@@ -44,7 +44,19 @@ MUTANTS = {
                                   "for (int a = 0; a < k; ++a) B[(size_t)tgt * p + a] = rhs[a];"),
     "B_transposed_store": ("for (int a = 0; a < k; ++a) B[(size_t)tgt * p + K[a]] = rhs[a];",
                            "for (int a = 0; a < k; ++a) B[(size_t)K[a] * p + tgt] = rhs[a];"),
+    # a wrong partner set in FindRoot (Algorithm 2): the variable at position 0 of U is
+    # never used as a partner
+    "partner_set_drops_first": ("            if (b == a) continue;", "            if (b == a || b == 0) continue;"),
+    # RegressRoot (Algorithm 1) skips the first remaining variable
+    "regress_root_skips_first": ("for (int a = 0; a < r && st == ORACLE_OK; ++a) {\n            int w = U[a];",
+                                 "for (int a = 1; a < r && st == ORACLE_OK; ++a) {\n            int w = U[a];"),
 }
+
+# Mutants that the brute-force pin (every score of every iteration on p <= 6) must catch
+# by itself: the score definition, the partner set and the data update between iterations.
+BRUTE_FORCE_MUTANTS = ("partner_set_drops_first", "regress_root_skips_first", "no_regress_root",
+                       "regress_root_backwards", "score_keeps_positive_part", "score_not_squared",
+                       "transposed_I", "swapped_residual", "drop_k2_term", "beta_sign", "gauss_kernel_exponent")
 
 
 def _pin_calls():
@@ -74,17 +86,36 @@ def tmpdir_mut():
         yield d
 
 
-@pytest.mark.parametrize("mutant", sorted(MUTANTS))
-def test_pins_catch_mutant(mutant, tmpdir_mut):
+def _mutant_view(mutant, tmpdir_mut):
+    """The oracle with one planted mistake, built into a temporary library."""
     old, new = MUTANTS[mutant]
     src = open(SRC).read()
     assert src.count(old) >= 1, f"mutation site of {mutant} not found"
     path_c = os.path.join(tmpdir_mut, f"{mutant}.c")
     path_so = os.path.join(tmpdir_mut, f"lib{mutant}.so")
-    open(path_c, "w").write(src.replace(old, new))
-    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-pthread", "-std=c11", "-D_GNU_SOURCE",
-                           "-ffp-contract=off", "-o", path_so, path_c, "-lm"])
-    view = omod.View(omod.load(path_so))
+    if not os.path.exists(path_so):
+        open(path_c, "w").write(src.replace(old, new))
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-pthread", "-std=c11", "-D_GNU_SOURCE",
+                               "-ffp-contract=off", "-o", path_so, path_c, "-lm"])
+    return omod.View(omod.load(path_so))
+
+
+@pytest.mark.parametrize("mutant", BRUTE_FORCE_MUTANTS)
+def test_brute_force_pin_catches_mutant(mutant, tmpdir_mut):
+    view = _mutant_view(mutant, tmpdir_mut)
+    caught = False
+    for case in pins._BRUTE_CASES:
+        try:
+            pins.test_every_score_of_every_iteration_by_brute_force(view, *case)
+        except Exception:
+            caught = True
+            break
+    assert caught, f"the brute-force pin missed mutant {mutant}"
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS))
+def test_pins_catch_mutant(mutant, tmpdir_mut):
+    view = _mutant_view(mutant, tmpdir_mut)
     caught = []
     for name, call in _pin_calls():
         try:

@@ -338,3 +338,71 @@ def test_variable_scores_match_fit(oracle_mod):
         vs = alive[::3]
         got = oracle_mod.variable_scores(d.X, order[:k], vs)
         assert np.allclose(got, S[k, vs], rtol=1e-12, atol=1e-18)
+
+
+# ---------------------------------------------------------------- brute force on p <= 6 (Algorithms 1-2)
+
+# The printed constants of Eq. HApp, typed here again so that this check shares no value
+# with the oracle's source.
+_K1, _K2, _BETA = 79.047, 7.4129, 0.37457
+_H_NU = 0.5 * (1.0 + math.log(2.0 * math.pi))
+
+
+def _naive_directlingam(X):
+    """DirectLiNGAM written out directly in numpy, with no intermediate reuse: at every
+    iteration, for every ordered pair (i, j) of the remaining variables, both rows are
+    normalised (mean, sample sd with divisor n - 1), each is regressed on the other
+    (slope = sample covariance / sample variance, np.cov), both residuals normalised,
+    I = H(x_j) + H(r_i) - H(x_i) - H(r_j) (Eq. Itest with Eq. HApp) and
+    S_i += min(0, I)^2 (Algorithm 2); the root is the argmin, lowest index on ties; every
+    remaining row is then regressed on the root's row (RegressRoot, Algorithm 1).
+    Returns the order and the p x p score matrix (NaN for removed variables)."""
+    W = np.array(X, dtype=np.float64)
+    p = W.shape[0]
+
+    def norm(v):
+        return (v - v.mean()) / v.std(ddof=1)
+
+    def H(u):
+        return _H_NU - _K1 * (np.mean(np.log(np.cosh(u))) - _BETA) ** 2 - _K2 * np.mean(u * np.exp(-u * u / 2)) ** 2
+
+    U = list(range(p))
+    order, S_all = [], np.full((p, p), np.nan)
+    for it in range(p):
+        for i in U:
+            s = 0.0
+            for j in U:
+                if j == i:
+                    continue
+                xi, xj = norm(W[i]), norm(W[j])
+                c = np.cov(xi, xj)
+                ri = norm(xi - c[0, 1] / c[1, 1] * xj)
+                rj = norm(xj - c[0, 1] / c[0, 0] * xi)
+                I = H(xj) + H(ri) - H(xi) - H(rj)
+                s += min(0.0, I) ** 2
+            S_all[it, i] = s
+        root = min(U, key=lambda v: (S_all[it, v], v))
+        order.append(root)
+        U.remove(root)
+        for w in U:
+            c = np.cov(W[w], W[root])
+            W[w] = W[w] - c[0, 1] / c[1, 1] * W[root]
+    return np.array(order), S_all
+
+
+_BRUTE_CASES = [(3, 2000, 11), (4, 3000, 12), (5, 4000, 13), (6, 5000, 14), (6, 2500, 15)]
+
+
+@pytest.mark.parametrize("p,n,seed", _BRUTE_CASES)
+def test_every_score_of_every_iteration_by_brute_force(oracle_mod, p, n, seed):
+    """North-star pin: on seeded p <= 6 DAGs every S_i of every iteration, recomputed by the
+    naive formula above, equals the oracle's within 1e-12 (absolute), and so does the order."""
+    d = synth.lingam_dataset(p, n, 0.6, seed=seed)
+    order_b, S_b = _naive_directlingam(d.X)
+    order_o, _, S_o = oracle_mod.fit(d.X, want_B=False)
+    assert list(order_o) == list(order_b)
+    m = ~np.isnan(S_b)
+    assert np.array_equal(m, ~np.isnan(S_o))
+    assert np.max(np.abs(S_o[m] - S_b[m])) <= 1e-12
+    assert np.all(S_b[m] >= 0.0)
+    assert np.max(S_b[m]) > 1e-6          # the case exercises non-trivial scores
