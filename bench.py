@@ -43,11 +43,9 @@ L2_FLUSH_BYTES = 256 << 20
 # Pair kernel SFU roofline: per pair-sample 4 ex2 (32 per SM per clock on sm_103a)
 # plus 2 lg2 per 32 samples (16 per SM per clock).
 SFU_CLK_PER_PAIR_SAMPLE = 4.0 / 32.0 + (2.0 / 32.0) / 16.0
-# DRAM bytes (read + write) per launch of the iteration kernel, from one ncu capture
-# of iterations 2 and 3 of a p = 1000, n = 1e4 fit (cold caches: the 40 MB of
-# normalised rows and the 8 MB covariance read once).  Valid for this kernel
-# version only: set to None when the kernel changes, until it is captured again.
-ITER_TRAFFIC_BYTES = 48.60e6 + 7.60e6
+# DRAM bytes (read + write) per launch of the iteration kernel, from an ncu capture of
+# the current kernel version (profiles/); None until the current version is captured.
+ITER_TRAFFIC_BYTES = None
 
 
 def unpruned_pair_samples(p: int, n: int) -> float:
@@ -194,8 +192,8 @@ def batched_workload(lingam, synth, torch, dev, stream, reps: int = 5) -> dict:
     """The batched configuration: 256 bootstrap resamples of one p=50, n=2000 dataset
     and 64 datasets with p in 20..120, n in 500..8000 (FP32, mixed path), each set one
     library call; inputs resident on the device; after two calls (eager, graph capture)
-    the replayed graph is timed with CUDA events.  Next to it, sequential single fits of
-    16 members of each set (one workspace per shape reused), scaled to the whole set."""
+    the replayed graph is timed with CUDA events.  Next to it, every member of each set as
+    a sequential single fit through lingam_fit (one workspace reused), timed as a whole."""
     import ctypes
     d = synth.lingam_dataset(50, 2000, 4.0 / 49.0, seed=5)
     X = torch.tensor(d.X.astype(np.float32), device=dev)
@@ -229,8 +227,8 @@ def batched_workload(lingam, synth, torch, dev, stream, reps: int = 5) -> dict:
     ru = lingam.fit_batch(Xs, workspace=wsu, want_report=True)
     ps_boot = sum(float(np.sum(pp)) * 2000 for pp in rb.pairs)
     ps_unev = sum(float(np.sum(pp)) * x.shape[1] for pp, x in zip(ru.pairs, Xs))
-    # sequential single fits of 16 members of each set
-    Xb = [X[:, idx[b].long()].contiguous() for b in range(16)]
+    # every member as a sequential single fit (one workspace of the largest size, reused)
+    Xb = [X[:, idx[b].long()].contiguous() for b in range(idx.shape[0])]
     ws1 = lingam.alloc_workspace(lingam.workspace_size(50, 2000), device=dev)
     for x in Xb[:2]:
         lingam.fit(x, workspace=ws1)
@@ -241,24 +239,125 @@ def batched_workload(lingam, synth, torch, dev, stream, reps: int = 5) -> dict:
         lingam.fit(x, workspace=ws1)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    seq_boot = e0.elapsed_time(e1) / 16 * 256
-    wsm = lingam.alloc_workspace(max(lingam.workspace_size(x.shape[0], x.shape[1]) for x in Xs[:16]), device=dev)
+    seq_boot = e0.elapsed_time(e1)
+    wsm = lingam.alloc_workspace(max(lingam.workspace_size(x.shape[0], x.shape[1]) for x in Xs), device=dev)
     lingam.fit(Xs[0], workspace=wsm)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for x in Xs[:16]:
+    for x in Xs:
         lingam.fit(x, workspace=wsm)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    seq_unev = e0.elapsed_time(e1) / 16 * 64
+    seq_unev = e0.elapsed_time(e1)
     return {"workload": "256 bootstrap resamples of p=50, n=2000 + 64 datasets p in 20..120, n in 500..8000",
             "bootstrap_256_ms": t_boot, "uneven_64_ms": t_unev,
-            "sequential_single_fits_estimate_ms": {"bootstrap_256": seq_boot, "uneven_64": seq_unev},
+            "sequential_single_fits_ms": {"bootstrap_256": seq_boot, "uneven_64": seq_unev},
             "speedup_vs_sequential": {"bootstrap_256": seq_boot / t_boot, "uneven_64": seq_unev / t_unev},
             "pair_samples_evaluated": {"bootstrap_256": ps_boot, "uneven_64": ps_unev},
             "pair_samples_per_s": {"bootstrap_256": ps_boot / (t_boot / 1e3), "uneven_64": ps_unev / (t_unev / 1e3)},
             "timing": "median of 5 graph replays, CUDA events; inputs on the device"}
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def configs_table(lingam, synth, torch, dev, stream, seeds=(1, 2, 3, 4, 5), reps: int = 3) -> dict:
+    """The five benchmark configurations over dataset seeds 1-5: fit time (median of
+    `reps`, CUDA events, inputs on the device), pairs evaluated, and for the single-dataset
+    configurations the FP64 GPU path on the same data (config 5: its first 5 iterations
+    against the mixed path's first 5) and whether the two paths' orders agree."""
+    def timed(fn):
+        fn()
+        out = []
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            out.append(e0.elapsed_time(e1))
+        return float(np.median(out)), r
+
+    table = {}
+    for name, dt_in in (("p20_n2000", np.float64), ("p100_n10000", np.float32), ("p300_n5000", np.float32),
+                        ("p1000_n10000", np.float32)):
+        rows = []
+        for seed in seeds:
+            d = synth.workload(name, seed=seed)
+            p, n = d.X.shape
+            row = {"seed": seed}
+            X64 = torch.tensor(d.X.astype(np.float32).astype(np.float64) if dt_in == np.float32 else d.X, device=dev)
+            k = 5 if p >= 1000 else 0
+            if dt_in == np.float32:
+                X32 = torch.tensor(d.X.astype(np.float32), device=dev)
+                ws = lingam.alloc_workspace(lingam.workspace_size(p, n), device=dev)
+                row["mixed_ms"], rm = timed(lambda: lingam.fit(X32, workspace=ws))
+                row["mixed_pairs"] = int(rm.pairs_total)
+                if k:
+                    row["mixed_first5_ms"], rm5 = timed(lambda: lingam.fit(X32, workspace=ws, max_iters=k))
+            ws64 = lingam.alloc_workspace(lingam.workspace_size(p, n, "fp64", np.float64), device=dev)
+            row["fp64_ms" if not k else "fp64_first5_ms"], r64 = timed(
+                lambda: lingam.fit(X64, precision="fp64", workspace=ws64, max_iters=k))
+            if dt_in == np.float32:
+                row["orders_agree"] = bool(np.array_equal((rm5 if k else rm).order[:k or p], r64.order[:k or p]))
+            rows.append(row)
+            del ws64
+        table[name] = rows
+    boot, unev = [], []
+    for seed in seeds:
+        d = synth.lingam_dataset(50, 2000, 4.0 / 49.0, seed=4 + seed)
+        X = torch.tensor(d.X.astype(np.float32), device=dev)
+        idx = torch.tensor(synth.bootstrap_indices(2000, 256, seed=5 + seed), device=dev)
+        ws = lingam.alloc_workspace(lingam.load().lingam_workspace_size_bootstrap(
+            50, 2000, 256, __import__("ctypes").byref(lingam.make_opts()[0])), device=dev)
+        lingam.fit_bootstrap(X, idx, workspace=ws)
+        boot.append(timed(lambda: lingam.fit_bootstrap(X, idx, workspace=ws))[0])
+        ds = synth.uneven_batch(64, seed=6 + seed)
+        Xs = [torch.tensor(dd.X.astype(np.float32), device=dev) for dd in ds]
+        wsu = lingam.batch_workspace([x.shape[0] for x in Xs], [x.shape[1] for x in Xs])
+        lingam.fit_batch(Xs, workspace=wsu)
+        unev.append(timed(lambda: lingam.fit_batch(Xs, workspace=wsu))[0])
+    table["batched"] = {"bootstrap_256_ms": boot, "uneven_64_ms": unev}
+    return table
+
+
+def scalability_sweep(lingam, synth, torch, dev, stream, reps: int = 3) -> list:
+    """The paper's scalability experiment (Sec. V-D): sparse and dense synthetic graphs
+    (synth.scalability_dataset) for p in {100, 200, 500, 1000} and n in {1024, 2048, 4096,
+    8192}, seed 1, FP32 data, mixed path with pruning and reuse: full lingam_fit time
+    (median of `reps` after one untimed call, CUDA events, inputs on the device) and the
+    fraction of pairs the threshold saved."""
+    rows = []
+    for dense in (False, True):
+        for p in (100, 200, 500, 1000):
+            for n in (1024, 2048, 4096, 8192):
+                d = synth.scalability_dataset(p, n, dense, seed=1)
+                X = torch.tensor(d.X.astype(np.float32), device=dev)
+                ws = lingam.alloc_workspace(lingam.workspace_size(p, n), device=dev)
+                r = lingam.fit(X, workspace=ws)
+                ts = []
+                for _ in range(reps):
+                    torch.cuda.synchronize(dev)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    lingam.fit(X, workspace=ws)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    ts.append(e0.elapsed_time(e1))
+                rows.append({"graph": "dense" if dense else "sparse", "p": p, "n": n,
+                             "fit_ms": float(np.median(ts)), "pairs_evaluated": int(r.pairs_total),
+                             "pruned_fraction": 1.0 - r.pairs_total / r.pairs_unpruned})
+                del ws, X
+    return rows
 
 
 def run_ours(args, rank: int, world: int):
@@ -288,8 +387,8 @@ def run_ours(args, rank: int, world: int):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def step(inp, out=None):
-        return lingam.fit(inp, precision="mixed", workspace=ws, timing=True, out=out, max_iters=args.max_iters,
+    def step(inp, out=None, timing=False):
+        return lingam.fit(inp, precision="mixed", workspace=ws, timing=timing, out=out, max_iters=args.max_iters,
                           want_B=args.max_iters == 0)
 
     for _ in range(args.warmup):
@@ -298,7 +397,8 @@ def run_ours(args, rank: int, world: int):
     props = torch.cuda.get_device_properties(dev)
     bus = getattr(props, "pci_bus_id", None)
     bus_id = f"{bus:02x}:00" if isinstance(bus, int) else None
-    step_ms, pair_ms, pairs, launches, phases = [], [], [], [], []
+    # the timed steps run the library as shipped (no per-launch events, no phase timers)
+    step_ms, pairs, launches = [], [], []
     with ClockSampler(bus_id) as clk:
         for _ in range(args.steps):
             flush.zero_()
@@ -309,11 +409,19 @@ def run_ours(args, rank: int, world: int):
             e1.record(stream)
             torch.cuda.synchronize(dev)
             step_ms.append(e0.elapsed_time(e1))
-            pair_ms.append(res.times_ms["pair"])
-            phases.append((res.times_ms["compute"], res.times_ms["merge"], res.times_ms["remove"]))
             pairs.append(res.pairs_total)
             launches.append(res.kernel_launches)
     clocks = clk.summary()
+    # a separate pass with the library's instrumentation on: the iteration kernel's launch
+    # times (CUDA events on the launching stream, one after each launch) for the roofline,
+    # and CTA 0's phase timers
+    pair_ms, phases = [], []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        rt = step(X, timing=True)
+        pair_ms.append(rt.times_ms["pair"])
+        phases.append((rt.times_ms["compute"], rt.times_ms["merge"], rt.times_ms["remove"]))
     barrier()
     tot_ms = max_over_ranks(float(np.sum(step_ms)), dist, dev)
     ms_per_step = tot_ms / args.steps
@@ -344,17 +452,19 @@ def run_ours(args, rank: int, world: int):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     nsm = props.multi_processor_count
     peak = nsm * (1.0 / SFU_CLK_PER_PAIR_SAMPLE) * sm_max * 1e6
-    achieved = float(np.sum(pairs)) * n / (float(np.sum(pair_ms)) / 1000.0)
+    achieved = float(np.mean(pairs)) * n / (float(np.mean(pair_ms)) / 1000.0)
     traffic = ITER_TRAFFIC_BYTES if (p, n) == (P_DEFAULT, N_DEFAULT) else None
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-samples/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_basis": "ncu dram__bytes_read+write of one launch (iteration 2 of a fit, cold caches)",
                 "kernel": "k_iteration<float>",
+                "timing_basis": "separate instrumented pass (one CUDA event after each launch); the timed steps run "
+                                "without instrumentation",
                 "peak_basis": f"SFU: 4 ex2 + 1/16 lg2 per pair-sample, {nsm} SMs x 32 ex2/clk at sm_max {sm_max:.0f} MHz"}
     # the same work over the pair-compute phases of the waves alone (device timer; the rest
     # of each launch is merging, wave finalisation, removal and grid barriers)
     ph = np.mean(np.array(phases), axis=0)
-    comp = float(np.sum(pairs)) * n / (float(np.sum([x[0] for x in phases])) / 1000.0)
+    comp = float(np.mean(pairs)) * n / (float(np.mean([x[0] for x in phases])) / 1000.0)
     roofline["compute_phase"] = {"achieved": comp / 1e9, "frac": comp / peak,
                                  "ms_per_step": {"pair_compute": ph[0], "merge_finalize": ph[1], "removal": ph[2]}}
 
@@ -393,12 +503,25 @@ def run_ours(args, rank: int, world: int):
         line["batched"] = batched_workload(lingam, synth, torch, dev, stream)
         line["batched"]["frac_of_xu_bound"] = {k: v / peak for k, v in line["batched"]["pair_samples_per_s"].items()}
 
+    if world == 1 and args.configs:
+        line["configs"] = configs_table(lingam, synth, torch, dev, stream)
+    if world == 1 and args.sweep:
+        line["scalability_sweep"] = scalability_sweep(lingam, synth, torch, dev, stream)
+
     if world == 1 and rank == 0 and not args.no_cpu:
+        import oracle
         X64 = d.X.astype(np.float32).astype(np.float64)
         rate, dt, m, cores = oracle_rate(X64, args.cpu_seconds)
+        # one core: the same FindRoot over a 40-variable subset
+        U1 = np.sort(np.random.default_rng(3).choice(p, min(p, 40), replace=False))
+        t1 = time.perf_counter()
+        oracle.find_root_scores(X64, U1, nthreads=1)
+        rate1 = len(U1) * (len(U1) - 1) / 2 * n / (time.perf_counter() - t1)
         line["cpu_baseline"] = {"value": rate, "unit": "pair-samples/s", "cores": cores, "kind": "oracle",
+                                "cpu_model": cpu_model(), "single_core_value": rate1,
                                 "sample": f"oracle FindRoot (Algorithm 2, every ordered pair) over {m} of the "
-                                          f"{p} variables of the same dataset, {dt:.1f} s"}
+                                          f"{p} variables of the same dataset, {dt:.1f} s; single core: 40 "
+                                          f"variables"}
     if dist is not None:
         dist.destroy_process_group()
     if rank == 0:
@@ -420,6 +543,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
     ap.add_argument("--max-iters", type=int, default=0, help="order only the first k iterations (profiling)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also run the paper's scalability grid (sparse/dense graphs, p x n)")
+    ap.add_argument("--configs", action="store_true",
+                    help="also time the five benchmark configurations over dataset seeds 1-5")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -77,8 +77,18 @@ typedef struct {
                                 those of the current iteration.  Used for iteration-by-iteration checks. */
     int max_iters;           /* 0 = all p iterations; else stop after this many (order[k] = -1 beyond,
                                 B is then not computed).  Used to time a bounded prefix of a run. */
-    int timing;              /* 1 = also time the pair-comparison phase of every iteration (report
-                                t_pair_ms); adds two CUDA events per iteration */
+    int timing;              /* 1 = also time every iteration's launch (report t_pair_ms and
+                                t_pair_iter_ms; one CUDA event recorded after each launch) and
+                                run the device phase timers (t_compute_ms ...); 0 for production */
+    const signed char* prior; /* NULL, or a p x p HOST matrix of prior knowledge (the paper notes
+                                that DirectLiNGAM accepts prior knowledge, Sec. II-C; read as known
+                                ancestors): prior[i*p + j] = 1 says X_j is known to be an ancestor
+                                of X_i; 0 or -1 say nothing to the ordering.  At every iteration
+                                only variables with no known ancestor left unordered may be the
+                                root; every remaining variable is still compared with them, and
+                                the scores of the others are reported as NaN.  Values other than
+                                -1, 0, 1, or a cycle among the known ancestors: LINGAM_EINVAL.
+                                Single fits only (lingam_fit, lingam_fit_static, lingam_autotune). */
 } lingam_opts;
 
 typedef struct {
@@ -100,9 +110,9 @@ typedef struct {
                                     launch of iteration k, between the stream events recorded after
                                     launch k - 1 (before the first launch) and after launch k */
     /* With opts.timing = 1 (single fits): device wall time (CTA 0's global timer, summed
-       over all iterations) of the pair-compute phases of the waves (each ends at a grid
-       barrier, so it covers the slowest CTA), of their merge and finalisation phases (each
-       ends when CTA 0 sees the wave's published result), and of CTA 0's part of the
+       over all iterations) of CTA 0's own pair-compute phases of the waves, of the rest of
+       each wave as CTA 0 sees it (the wait for the slower CTAs' tiles, the merge and the
+       finalisation, up to the wave's published result), and of CTA 0's part of the
        removals (UpdateData, UpdateCovMat).  0 otherwise. */
     double t_compute_ms, t_merge_ms, t_remove_ms;
 } lingam_report;
@@ -246,8 +256,12 @@ int lingam_fit_bootstrap(const void* X, long long p, long long n, int nboot, con
  * loaded on until the process exits.  It allocates nothing.
  *
  *   - Returns LINGAM_EINVAL when lingam_workspace_size(p, n, opts) exceeds
- *     LINGAM_STATIC_SCRATCH_BYTES (32 MiB: enough for the mixed path up to
- *     about p = 200, n = 10^4, or the FP64 path up to about p = 128, n = 10^4).
+ *     LINGAM_STATIC_SCRATCH_BYTES (32 MiB).  With the default options (and FP64
+ *     input for the FP64 path) that admits: the mixed path up to p = 128 at
+ *     n = 10^4, p = 217 at n = 5000, p = 430 at n = 1000; the FP64 path up to
+ *     p = 74 at n = 10^4, p = 136 at n = 5000, p = 333 at n = 1000.  The
+ *     workspace grows about linearly in n (the rows) and in p^2 (the
+ *     covariances), so lingam_workspace_size is the test for other sizes.
  *   - The first call on a device looks up the scratch array's device address
  *     (once per device, with that device current); make that first call before
  *     any stream capture on the device.

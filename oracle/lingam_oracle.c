@@ -325,6 +325,17 @@ int oracle_fit_B(const double* X, int p, long n, const int* K, double* B) {
 
 /* ---------------- Algorithm 1 ---------------- */
 
+/* Prior knowledge (the paper notes that DirectLiNGAM accepts prior knowledge, Sec. II-C; it
+ * is read here as known ancestors): prior[i*p + j] == 1 says that x_j is an ancestor of x_i.
+ * At every iteration only the variables of U with no known ancestor left in U can be the
+ * root; every variable of U stays a partner in the comparisons (Algorithm 2 unchanged). */
+static int is_candidate(const signed char* prior, int p, const int* U, int r, int a) {
+    if (!prior) return 1;
+    for (int b = 0; b < r; ++b)
+        if (b != a && prior[(size_t)U[a] * p + U[b]] == 1) return 0;
+    return 1;
+}
+
 /*
  * oracle_fit: DirectLiNGAM on X (p x n, row-major, not modified).
  *   order[p]       causal order K (0-based variable indices), order[0] first root.
@@ -335,8 +346,8 @@ int oracle_fit_B(const double* X, int p, long n, const int* K, double* B) {
  *                  (scores are still those of FindRoot on the current U).
  *   nthreads       threads for FindRoot (0 = all online cores).
  */
-int oracle_fit(const double* X, int p, long n, int* order, double* B, double* scores, const int* forced,
-               int nthreads) {
+static int fit_impl(const double* X, int p, long n, int* order, double* B, double* scores, const int* forced,
+                    const signed char* prior, int nthreads) {
     if (p < 1 || n < 3 || !X || !order) return ORACLE_EINVAL;
     double* W = (double*)malloc(sizeof(double) * (size_t)p * (size_t)n);
     int* U = (int*)malloc(sizeof(int) * (size_t)p);
@@ -353,12 +364,17 @@ int oracle_fit(const double* X, int p, long n, int* order, double* B, double* sc
         if (r == 1) S[0] = 0.0;
         else st = find_root_scores(W, U, r, n, p, nthreads, S);
         if (st != ORACLE_OK) break;
-        int best = 0;
-        for (int a = 1; a < r; ++a)
-            if (S[a] < S[best] || (S[a] == S[best] && U[a] < U[best])) best = a;
+        int best = -1;
+        for (int a = 0; a < r; ++a) {
+            if (!is_candidate(prior, p, U, r, a)) continue;
+            if (best < 0) best = a;
+            else if (S[a] < S[best] || (S[a] == S[best] && U[a] < U[best])) best = a;
+        }
+        if (best < 0) { st = ORACLE_EINVAL; break; }   /* a cycle among the known ancestors */
         if (scores) {
             for (int v = 0; v < p; ++v) scores[(size_t)it * p + v] = NAN;
-            for (int a = 0; a < r; ++a) scores[(size_t)it * p + U[a]] = S[a];
+            for (int a = 0; a < r; ++a)
+                if (is_candidate(prior, p, U, r, a)) scores[(size_t)it * p + U[a]] = S[a];
         }
         if (forced) {
             best = -1;
@@ -381,6 +397,19 @@ int oracle_fit(const double* X, int p, long n, int* order, double* B, double* sc
     if (st == ORACLE_OK && B) st = oracle_fit_B(X, p, n, order, B);
     free(W); free(U); free(S); free(tmp);
     return st;
+}
+
+int oracle_fit(const double* X, int p, long n, int* order, double* B, double* scores, const int* forced,
+               int nthreads) {
+    return fit_impl(X, p, n, order, B, scores, forced, NULL, nthreads);
+}
+
+/* oracle_fit with prior knowledge prior[p*p] (see is_candidate); scores of the variables
+ * that cannot be the root at an iteration are NaN. */
+int oracle_fit_prior(const double* X, int p, long n, const signed char* prior, int* order, double* B,
+                     double* scores, const int* forced, int nthreads) {
+    if (!prior) return ORACLE_EINVAL;
+    return fit_impl(X, p, n, order, B, scores, forced, prior, nthreads);
 }
 
 /* I for a list of (i, j) variable pairs of raw rows X (p x n), threaded. */

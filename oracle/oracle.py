@@ -75,6 +75,8 @@ def _declare(L):
     L.oracle_find_root_scores.argtypes = [dp, ctypes.c_int, ctypes.c_long, ip, ctypes.c_int, ctypes.c_int, dp]
     L.oracle_fit_B.argtypes = [dp, ctypes.c_int, ctypes.c_long, ip, dp]
     L.oracle_fit.argtypes = [dp, ctypes.c_int, ctypes.c_long, ip, dp, dp, ip, ctypes.c_int]
+    L.oracle_fit_prior.argtypes = [dp, ctypes.c_int, ctypes.c_long, ctypes.POINTER(ctypes.c_byte), ip, dp, dp, ip,
+                                   ctypes.c_int]
     L.oracle_pair_measures.argtypes = [dp, ctypes.c_long, ip, ip, ctypes.c_int, ctypes.c_int, dp]
     L.oracle_num_threads.argtypes = [ctypes.c_int]
     L.oracle_variable_scores.argtypes = [dp, ctypes.c_int, ctypes.c_long, ip, ctypes.c_int, ip, ctypes.c_int,
@@ -183,16 +185,26 @@ def fit_B(X, order, lib=None) -> np.ndarray:
     return B
 
 
-def fit(X, forced_order=None, want_scores: bool = True, want_B: bool = True, nthreads: int = 0, lib=None):
-    """Algorithm 1.  Returns (order, B or None, scores p x p or None)."""
+def fit(X, forced_order=None, want_scores: bool = True, want_B: bool = True, nthreads: int = 0, lib=None,
+        prior=None):
+    """Algorithm 1.  Returns (order, B or None, scores p x p or None).  prior (p x p, values
+    -1/0/1): prior[i, j] == 1 says x_j is a known ancestor of x_i; then only variables with
+    no known ancestor left are root candidates, the others' scores are NaN."""
     X = _rows(X)
     p, n = X.shape
     order = np.zeros(p, dtype=np.int32)
     B = np.zeros((p, p)) if want_B else None
     S = np.full((p, p), np.nan) if want_scores else None
     forced = None if forced_order is None else np.ascontiguousarray(forced_order, dtype=np.int32)
-    st = (lib or _get()).oracle_fit(_d(X), p, n, _i(order), _d(B) if B is not None else None,
-                           _d(S) if S is not None else None, _i(forced) if forced is not None else None, nthreads)
+    L = lib or _get()
+    args = (_d(X), p, n)
+    tail = (_i(order), _d(B) if B is not None else None, _d(S) if S is not None else None,
+            _i(forced) if forced is not None else None, nthreads)
+    if prior is None:
+        st = L.oracle_fit(*args, *tail)
+    else:
+        pr = np.ascontiguousarray(prior, dtype=np.int8)
+        st = L.oracle_fit_prior(*args, pr.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)), *tail)
     if st != OK:
         raise OracleError(st, "fit")
     return order, B, S

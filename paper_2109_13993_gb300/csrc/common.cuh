@@ -35,12 +35,16 @@ constexpr int kSampleAlign = 128;      // n is padded with zero samples to a mul
 // so a correlation within 2^-21 of +-1 cannot be told apart from an exact one.
 __host__ __device__ constexpr double degenerate_om(bool f32) { return f32 ? 0x1p-20 : 1e-14; }
 constexpr int kMaxSplit = 64;
+// CTAs of a pair-kernel launch at most (two per SM of a 152-SM GB300 fit under it); the
+// launches cap their grids at this bound, and the partial-moment slots of a wave (one per
+// tile and CTA segment) are sized by it.
+constexpr int kMaxGrid = 320;
 
-// Flags per variable (ctl->flags[v]).
+// Flags: per variable (Fit::flags) kAlive; per candidate position (Fit::cflag) the others.
 constexpr int kAlive = 1;      // still in U
 constexpr int kColumned = 2;   // was a column of a wave this iteration => complete
 constexpr int kDead = 4;       // partial score exceeded the best complete score
-constexpr int kPick = 8;       // chosen as a column of the next wave (transient)
+constexpr int kNoRoot = 8;     // a known ancestor is still in U (prior knowledge): never the root
 
 // ---------------------------------------------------------------------------
 // Per-fit control block in device memory.  Written by kernels, read by the
@@ -110,10 +114,19 @@ struct Fit {
     double* sd;          // [p] row standard deviations (divisor n-1)
     double* sig;         // [p x p] covariance of the normalised rows, downdated each iteration
     double* sig0;        // [p x p] covariance of the normalised rows before any removal
+    float2* sigf;        // [p x p] mixed path: {rho, 1 - rho^2} of sig, each formed in FP64 and
+                         // rounded once: the FP32 pair kernel's coefficients without FP64 work
     double* hx;          // [p] H(x_v) - H(nu) of the current normalised rows
-    double* part;        // [p] partial / full scores of the current iteration
-    double* prev;        // [p] scores of the previous iteration (ordering of candidates)
-    int* flags;          // [p]
+    float4* vstat;       // [p] per variable, for the FP32 pair path (see var_stats)
+    // The current iteration's candidates are indexed by their position k in the candidate
+    // list (sigma): part[k] is candidate k's partial score, its full score once complete;
+    // cflag[k] holds kColumned / kDead; crow[k] is its row slot in the current wave (-1 when
+    // it is not one of the wave's rows).  The plan starts them at 0, 0 and k.
+    double* part;        // [p] by candidate position
+    int* cflag;          // [p] by candidate position
+    int* crow;           // [p] by candidate position
+    double* prev;        // [p] scores of the previous iteration (ordering of candidates), by variable
+    int* flags;          // [p] by variable: kAlive while the variable is in U
     int* sigma;          // [p] alive variables in candidate order
     int* sigma_alt;      // [p] the next iteration's candidate order (single fits: planned
                          // during this iteration's removal; the host swaps the two per launch)
@@ -121,7 +134,10 @@ struct Fit {
     int* cols;           // [kTJ] columns of the current wave
     int* order;          // [p] causal order (device copy)
     const int* forced;   // [p] forced order or nullptr
-    int* scratch;        // [p] row list of the next wave (staging)
+    const signed char* prior;  // [p x p] prior knowledge (prior[i p + j] = 1: x_j a known ancestor of x_i) or nullptr
+    int* anc_cnt;        // [p] with prior: known ancestors of each variable still in U
+    int* scratch;        // [p] wave finalisation: row slots of candidates beyond its registers;
+                         // B fit: the Cholesky's row flags
     double* rowsum;      // [p] per row slot of the wave: sum over its columns of min(0, I)^2
     double* colsum;      // [maxtiles x kTJ] per tile and column: sum over the tile's rows of max(0, I)^2
     void* partials;      // [maxtiles x maxsplit x kPairThreads x 16] split partial moments (float or double)
@@ -146,6 +162,9 @@ struct Fit {
 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_status(Ctl* ctl, int code) { atomicCAS(&ctl->status, 0, code); }
+
+// The FP32 pair kernel's view of a covariance element (Fit::sigf).
+__device__ __forceinline__ float2 sig_pair_f(double rho) { return make_float2(float(rho), float(fma(-rho, rho, 1.0))); }
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -230,6 +249,28 @@ __host__ __device__ __forceinline__ double hterm(double lcc, double g, double n)
 __host__ __device__ __forceinline__ float hterm_f(float lcc, float g, float inv_n) {
     const float a = lcc * inv_n, b = g * inv_n;
     return -float(kK1) * a * a - float(kK2) * b * b;
+}
+
+// Statistics of one normalised row that the FP32 pair path needs, from the row's FP64
+// moment sums L = sum_t (log cosh u_t - beta) and Gs = sum_t u_t exp(-u_t^2/2) over its n
+// samples (row length ld with zero padding):
+//   .w  the offset -kSub (ln 2 + m) of a 32-sample group, in FP32, m = mean log cosh.  The
+//       pair kernel centres a residual's log-cosh group sums by its variable's own mean
+//       (instead of beta), so that the FP32 sums stay small also for strongly
+//       non-Gaussian variables;
+//   .x  corr = (m (ld - n) - (ld / kSub) eps) / n, eps = the FP32 rounding of .w: for a
+//       residual whose centred sum over the padded row is T, its mean log cosh exceeds m by
+//       delta = T / n + corr exactly (padding samples have log cosh 0);
+//   .y  2 (m - beta) and .z  the mean of u exp(-u^2/2), with which the entropy difference of
+//       Eq. HApp between a residual and its variable is formed without the large terms:
+//       H(r) - H(x) = -k1 delta (2 (m - beta) + delta) - k2 (gr - g)(gr + g).
+__host__ __device__ inline float4 var_stats(double L, double Gs, int n, int ld) {
+    const double m = kBeta + L / double(n);
+    const double g = Gs / double(n);
+    const float off = float(-double(kSub) * (kLn2 + m));
+    const double eps = double(off) + double(kSub) * (kLn2 + m);
+    const double corr = (m * double(ld - n) - double(ld / kSub) * eps) / double(n);
+    return make_float4(float(corr), float(2.0 * (m - kBeta)), float(g), off);
 }
 
 }  // namespace lingam

@@ -346,6 +346,9 @@ __global__ void k_gram_tc_reduce(Fit f, const float2* __restrict__ partial, cons
         f.sig[size_t(j) * p + i] = v;
         f.sig0[size_t(i) * p + j] = v;
         f.sig0[size_t(j) * p + i] = v;
+        const float2 vf = sig_pair_f(v);
+        f.sigf[size_t(i) * p + j] = vf;
+        f.sigf[size_t(j) * p + i] = vf;
     }
 }
 

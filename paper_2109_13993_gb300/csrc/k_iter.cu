@@ -193,6 +193,15 @@ struct FF {
     __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };
 
+// Sum of two float-float values (hi, lo): TwoSum of the high parts, the low parts added to
+// its error, renormalised.  About 48 bits, in FP32 arithmetic.
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    const float s = a.x + b.x, bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (b.x - bb) + (a.y + b.y);
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+
 // 16 consecutive values (16-byte aligned) through L2.
 __device__ __forceinline__ void load16_cg(float* v, const float* src) {
 #pragma unroll
@@ -360,11 +369,35 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
         __syncthreads();
         fence_proxy_async();   // this shared memory is the copy ring of later phases
     }
-    for (int k = tid; k < r; k += NTH) {
-        const int v = sigma[k];
-        f.part[v] = 0.0;
-        f.flags[v] = kAlive;
-        f.rows[k] = v;
+    // Prior knowledge: only variables with no known ancestor left in U can be the root; they
+    // go first (a stable partition of the candidate order), the others are flagged kNoRoot
+    // and take part as rows only.
+    int ncand = r;
+    if (f.prior && r > 1) {
+        int* tmp = reinterpret_cast<int*>(smem);   // r <= kMaxP ints fit the copy ring
+        for (int k = tid; k < r; k += NTH) tmp[k] = sigma[k];
+        __syncthreads();
+        int out = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int base = 0; base < r; base += NTH) {
+                const int k = base + tid;
+                const int v = k < r ? tmp[k] : -1;
+                const int c = v >= 0 && ((ld2(f.anc_cnt + v) == 0) == (pass == 0));
+                int tot;
+                const int rank = out + scan01<NTH>(c, red, &tot);
+                if (c) sigma[rank] = v;
+                out += tot;
+                __syncthreads();
+            }
+            if (pass == 0) ncand = out;
+        }
+        fence_proxy_async();   // this shared memory is the copy ring of later phases
+    }
+    for (int k = tid; k < r; k += NTH) {   // candidate state by position; the first wave's rows
+        f.part[k] = 0.0;
+        f.cflag[k] = k < ncand ? 0 : kNoRoot;
+        f.crow[k] = k;
+        f.rows[k] = sigma[k];
     }
     if (f.want_scores)
         for (int v = tid; v < p; v += NTH) f.rep_scores[size_t(it) * p + v] = NAN;
@@ -392,7 +425,7 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
             ctl->ncol = ctl->nrow = ctl->ntiles = 0;
         } else {
             ctl->done = 0;
-            const int nc = r < TJ ? r : TJ;
+            const int nc = ncand < TJ ? ncand : TJ;
             for (int c = 0; c < nc; ++c) f.cols[c] = sigma[c];
             ctl->ncol = nc;
             ctl->nrow = r;
@@ -401,60 +434,84 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
     }
 }
 
+// Scores are sums of squares, so they are >= 0 (or +inf): their IEEE-754 bit patterns order
+// like the integers they read as, and the finalisation compares them as integers instead of
+// in FP64 (which runs at a small fraction of the FP32 rate on this GPU).
+__device__ __forceinline__ long long okey(double x) { return __double_as_longlong(x); }
+
 // ------------------------------------------------------------------ wave finalisation
 // The wave a phase works on: its tiles, columns and rows.
 struct Wave {
     int ntiles, ncol, nrow;
 };
 
-// Run by one CTA (the one that merged the wave's last tile).
+// Run by one CTA (the one that merged the wave's last tile).  The candidates' state is
+// indexed by position in the candidate list, so this CTA reads it contiguously (two
+// dependent round trips in all: the state, then the rows' contributions by row slot) and
+// holds kPre positions per thread in registers; positions beyond kPre NTH (r > 4096 at 512
+// threads) go through global memory instead.
 template <int NTH, int TI, int TJ>
 __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it, int* red, unsigned seq) {
     Ctl* ctl = f.ctl;
     volatile Ctl* vc = ctl;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ncol = wv.ncol, nrow = wv.nrow, ntiles = wv.ntiles;
     const int p = f.p, r = vc->r;
+    const bool reuse = f.reuse != 0;
+    constexpr int NW = NTH / 32;
     constexpr int PARTS = NTH / 64;
     constexpr int SL = NTH / TJ;   // slices of the column parts
-    static_assert(SL <= 32, "slices fit the staging array");
-    static_assert(TJ <= 32 && NTH >= 64, "the wave's columns are threads 0 .. TJ - 1");
-    constexpr int kPre = 8;        // candidate positions per thread fetched ahead (r <= kPre * NTH)
+    static_assert(SL <= 32 && NW <= 32, "slices and warps fit the staging arrays");
+    static_assert(TJ <= 32 && NTH >= 64, "the wave's column totals are threads 0 .. TJ - 1");
+    constexpr int kPre = 8;        // candidate positions per thread held in registers
+    const int nblk = (r + NTH - 1) / NTH;
     __shared__ double s_col[32 * 33];
-    __shared__ double s_best;
+    __shared__ double s_tot[32];
+    __shared__ double s_best, s_rootpt;
     __shared__ int s_bestv;
+    __shared__ double s_csc[32];   // the wave's complete scores, by column
+    __shared__ int s_cv[32];       // and their variables
 
-    // Every load that depends on nothing written in this finalisation is issued first:
-    // the candidates in order, this thread's slice of the column parts, the columns, the
-    // running threshold and pair count.
-    int pv[kPre];
+    // 1. Every load that depends on nothing written here: per candidate position k = j NTH + tid
+    //    its variable, score, flags and row slot; this thread's slice of the column parts; the
+    //    running threshold and pair count.
+    int pv[kPre], pfl[kPre], prw[kPre];
+    double ppt[kPre];
 #pragma unroll
     for (int j = 0; j < kPre; ++j) {
         const int k = j * NTH + tid;
-        pv[j] = k < r ? ld2(f.sigma + k) : -1;
+        const bool in = k < r;
+        pv[j] = in ? ld2(f.sigma + k) : -1;
+        ppt[j] = in ? ld2(f.part + k) : 0.0;
+        pfl[j] = in ? ld2(f.cflag + k) : 0;
+        prw[j] = in ? ld2(f.crow + k) : -1;
     }
-    // thread (slice sl, column c) sums parts sl, sl + SL, ... of column c in that order
+    // thread (slice sl, column c) sums parts sl, sl + SL, ... of column c in that order; the
+    // FP32 path's parts are float-float pairs summed in FP32 arithmetic, the FP64 path's doubles
     const int nparts = ntiles * PARTS;
+    const bool ffparts = f.precision == LINGAM_MIXED;
     double ps = 0.0;
+    float2 psf = make_float2(0.f, 0.f);
     {
         const int c = tid % TJ, sl = tid / TJ;
         constexpr int kB = 8;
-        int tp = sl;
-        for (; tp + (kB - 1) * SL < nparts; tp += kB * SL) {
+        for (int tp = sl; tp < nparts; tp += kB * SL) {
             double v[kB];
 #pragma unroll
-            for (int q = 0; q < kB; ++q) v[q] = ld2(f.colsum + size_t(tp + q * SL) * TJ + c);
+            for (int q = 0; q < kB; ++q) {
+                const int at = tp + q * SL;
+                v[q] = at < nparts ? ld2(f.colsum + size_t(at) * TJ + c) : 0.0;
+            }
+            if (ffparts) {
 #pragma unroll
-            for (int q = 0; q < kB; ++q) ps += v[q];
+                for (int q = 0; q < kB; ++q)
+                    if (tp + q * SL < nparts) psf = ff_add(psf, *reinterpret_cast<const float2*>(&v[q]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < kB; ++q)
+                    if (tp + q * SL < nparts) ps += v[q];
+            }
         }
-        for (; tp < nparts; tp += SL) ps += ld2(f.colsum + size_t(tp) * TJ + c);
-    }
-    int cv = 0x7fffffff, cfl = 0;
-    double cpart = 0.0;
-    if (tid < ncol) {
-        cv = ld2(f.cols + tid);
-        cpart = ld2(f.part + cv);
-        cfl = ld2(f.flags + cv);
     }
     double best0 = INFINITY;
     int bv0 = -1;
@@ -464,59 +521,85 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
         bv0 = vc->best_var;
         pairs0 = vc->pairs_it;
     }
-
-    // 1. row contributions min(0, I(row, col))^2 summed over the wave's columns.  The
-    //    columns are rows 0 .. ncol - 1 (thread e holds row e < ncol): their sums join
-    //    the column totals in step 3, in the same order of additions.
-    double col_rs = 0.0;
-    if (f.reuse) {
-#pragma unroll 4
-        for (int e = tid; e < nrow; e += NTH) {
-            const int v = ld2(f.rows + e);
-            const double add = ld2(f.rowsum + e);
-            if (e < ncol)
-                col_rs = add;
-            else
-                f.part[v] = ld2(f.part + v) + add;
+    // 2. the row contribution min(0, I(row, col))^2 summed over the wave's columns, of every
+    //    candidate that is a row of this wave (by its row slot)
+    double add[kPre];
+#pragma unroll
+    for (int j = 0; j < kPre; ++j) add[j] = (reuse && prw[j] >= 0) ? ld2(f.rowsum + prw[j]) : 0.0;
+    // 3. column contributions max(0, I(row, col))^2 = min(0, I(col, row))^2: the slice sums of
+    //    a column added in slice order (a fixed order)
+    if (ffparts) {
+        reinterpret_cast<float2*>(s_col)[(tid / TJ) * 33 + tid % TJ] = psf;
+    } else {
+        s_col[(tid / TJ) * 33 + tid % TJ] = ps;
+    }
+    __syncthreads();
+    if (tid < TJ) {
+        if (ffparts) {
+            float2 tf = make_float2(0.f, 0.f);
+            for (int j = 0; j < SL; ++j) tf = ff_add(tf, reinterpret_cast<const float2*>(s_col)[j * 33 + tid]);
+            s_tot[tid] = double(tf.x) + double(tf.y);
+        } else {
+            double tot = 0.0;
+            for (int j = 0; j < SL; ++j) tot += s_col[j * 33 + tid];
+            s_tot[tid] = tot;
         }
     }
-    // 2. column contributions max(0, I(row, col))^2 = min(0, I(col, row))^2: the slice
-    //    sums of a column added in slice order (a fixed order)
-    s_col[(tid / TJ) * 33 + tid % TJ] = ps;
     __syncthreads();
-    double tot = 0.0;
-    if (tid < TJ)
-        for (int j = 0; j < SL; ++j) tot += s_col[j * 33 + tid];
-    // 3. the columns' complete scores; threshold = lowest complete score (lowest variable
-    //    index on ties)
-    if (tid < 32) {
-        double sc = INFINITY;
-        int v = 0x7fffffff;
-        if (tid < ncol) {
-            v = cv;
-            sc = (f.reuse ? cpart + col_rs : cpart) + tot;
-            f.part[v] = sc;
-            f.flags[v] = cfl | kColumned;
-            if (f.want_scores) f.rep_scores[(size_t)it * p + v] = sc;
+    // 4. a column of this wave (row slot c < ncol is column c) is complete: its score so far,
+    //    its own row's contribution (reuse), then its column total; the other rows add their
+    //    contribution.  Lowest complete score of the wave, lowest variable index on ties.
+    auto score_one = [&](int v, int e, double& pt, int& fl, double a) {
+        if (e >= 0 && e < ncol) {
+            const double sc = (reuse ? pt + a : pt) + s_tot[e];
+            pt = sc;
+            fl |= kColumned;
+            if (f.want_scores) f.rep_scores[size_t(it) * p + v] = sc;
+            s_csc[e] = sc;
+            s_cv[e] = v;
+        } else if (e >= 0 && reuse) {
+            pt = pt + a;
         }
+    };
+#pragma unroll
+    for (int j = 0; j < kPre; ++j)
+        if (pv[j] >= 0) score_one(pv[j], prw[j], ppt[j], pfl[j], add[j]);
+    for (int j = kPre; j < nblk; ++j) {   // positions beyond the registers
+        const int k = j * NTH + tid;
+        if (k >= r) continue;
+        const int v = ld2(f.sigma + k), e = ld2(f.crow + k);
+        double pt = ld2(f.part + k);
+        int fl = ld2(f.cflag + k);
+        const double a = (reuse && e >= 0) ? ld2(f.rowsum + e) : 0.0;
+        score_one(v, e, pt, fl, a);
+        f.part[k] = pt;
+        f.cflag[k] = fl;
+    }
+    __syncthreads();
+    if (tid < 32) {   // lowest complete score of the wave, lowest variable index on ties
+        long long kc = tid < ncol ? okey(s_csc[tid]) : 0x7fffffffffffffffll;
+        int vc = tid < ncol ? s_cv[tid] : 0x7fffffff;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double so = __shfl_xor_sync(0xffffffffu, sc, o);
-            const int vo = __shfl_xor_sync(0xffffffffu, v, o);
-            if (so < sc || (so == sc && vo < v)) {
-                sc = so;
-                v = vo;
+            const long long ko = __shfl_xor_sync(0xffffffffu, kc, o);
+            const int vo = __shfl_xor_sync(0xffffffffu, vc, o);
+            if (ko < kc || (ko == kc && vo < vc)) {
+                kc = ko;
+                vc = vo;
             }
         }
+        const double sc = __longlong_as_double(kc);
+        const int v = vc;
+        // threshold = lowest complete score of the iteration so far
+        if (tid == 0 && (bv0 < 0 || kc < okey(best0) || (kc == okey(best0) && v < bv0))) {
+            best0 = sc;
+            bv0 = v;
+            ctl->best = sc;
+            ctl->best_var = v;
+        }
         if (tid == 0) {
-            if (bv0 < 0 || sc < best0 || (sc == best0 && v < bv0)) {
-                best0 = sc;
-                bv0 = v;
-                ctl->best = sc;
-                ctl->best_var = v;
-            }
-            pairs0 += f.reuse ? (long long)ncol * (ncol - 1) / 2 + (long long)ncol * (nrow - ncol)
-                              : (long long)ncol * (nrow - 1);
+            pairs0 += reuse ? (long long)ncol * (ncol - 1) / 2 + (long long)ncol * (nrow - ncol)
+                            : (long long)ncol * (nrow - 1);
             ctl->pairs_it = pairs0;
             s_best = best0;
             s_bestv = bv0;
@@ -526,109 +609,102 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
     const double best = s_best;
     const int bv = s_bestv;
 
-    // 4. one pass over the candidates: prune (partial score above the threshold), pick
-    //    the next columns (the first TJ live un-columned variables in candidate order)
-    //    and list the next rows (every other row-eligible variable: un-columned ones with
-    //    reuse, all remaining ones without), both in candidate order.  The rows are
-    //    written where they belong when the next wave has TJ columns (rows TJ, TJ + 1,
-    //    ...) and also to scratch, from which a wave of fewer columns copies them.
-    int pfl[kPre];
-    double ppart[kPre];
-#pragma unroll
-    for (int j = 0; j < kPre; ++j) {
-        pfl[j] = pv[j] >= 0 ? ld2(f.flags + pv[j]) : 0;
-        ppart[j] = pv[j] >= 0 ? ld2(f.part + pv[j]) : 0.0;
-    }
-    int nlive = 0, nr = 0;
-    for (int base = 0, j = 0; base < r; base += NTH, ++j) {
-        const int k = base + tid;
-        int live = 0, elig = 0, v = -1, fl = 0;
-        double pt = 0.0;
-        if (k < r) {
-            if (j < kPre) {
-                v = pv[j];
-                fl = pfl[j];
-                pt = ppart[j];
-            } else {
-                v = ld2(f.sigma + k);
-                fl = ld2(f.flags + v);
-                pt = ld2(f.part + v);
-            }
-            const bool col = (fl & kColumned) != 0;
-            if (!col) {
-                if (!(fl & kDead) && f.prune && f.reuse && pt > best) {
-                    fl |= kDead;
-                    f.flags[v] = fl;
-                }
-                live = (fl & kDead) ? 0 : 1;
-            }
-            elig = f.reuse ? !col : 1;
-        }
+    // 5. prune (partial score above the threshold), pick the next columns (the first TJ live
+    //    un-columned candidates in candidate order) and rank the next rows (every other
+    //    row-eligible candidate: un-columned ones with reuse, all of them without), in
+    //    candidate order.  slot: a pick's column index; an eligible non-pick TJ + its rank
+    //    among the non-picks (final row slot nc + rank, once nc is known); else -1.
+    int slot[kPre];
+    int nlive = 0, nel = 0;   // live and eligible candidates in earlier blocks
+    auto rank_one = [&](int live, int elig, int& sl) {
         int pl, pe, tl, te;
-        // ranks among live and among eligible variables (a pick is live and eligible)
         scan01x2<NTH>(live, elig, red, &pl, &pe, &tl, &te);
         const int lrank = nlive + pl;
         const bool pick = live && lrank < TJ;
-        // every pick is eligible; the row rank of an eligible non-pick is the rows listed
-        // so far plus the eligible variables before it in this block minus the picks among them
-        const int picked_before = min(nlive + pl, TJ) - min(nlive, TJ);
-        if (pick) {
-            f.cols[lrank] = v;
-            f.rows[lrank] = v;
-        }
-        if (elig && !pick) {
-            const int ri = nr + pe - picked_before;
-            f.scratch[ri] = v;
-            f.rows[TJ + ri] = v;
-        }
-        const int picks_here = min(nlive + tl, TJ) - min(nlive, TJ);
+        sl = pick ? lrank : (elig ? TJ + (nel + pe - min(nlive + pl, TJ)) : -1);
         nlive += tl;
-        nr += te - picks_here;
-        __syncthreads();
+        nel += te;
+    };
+    auto prune_one = [&](int& fl, double pt, int& live, int& elig) {
+        const bool col = (fl & kColumned) != 0;
+        live = 0;
+        if (!col) {
+            if (!(fl & kDead) && f.prune && reuse && okey(pt) > okey(best)) fl |= kDead;
+            live = (fl & (kDead | kNoRoot)) ? 0 : 1;
+        }
+        elig = reuse ? !col : 1;
+    };
+#pragma unroll
+    for (int j = 0; j < kPre; ++j) {
+        if (j >= nblk) break;
+        int live = 0, elig = 0;
+        if (pv[j] >= 0) prune_one(pfl[j], ppt[j], live, elig);
+        rank_one(live, elig, slot[j]);
+    }
+    for (int j = kPre; j < nblk; ++j) {
+        const int k = j * NTH + tid;
+        int live = 0, elig = 0, sl = -1;
+        if (k < r) {
+            int fl = ld2(f.cflag + k);
+            prune_one(fl, ld2(f.part + k), live, elig);
+            f.cflag[k] = fl;
+        }
+        rank_one(live, elig, sl);
+        if (k < r) f.scratch[k] = sl;
     }
     const int nc = nlive < TJ ? nlive : TJ;
-    if (nc < TJ) {
-        for (int k = tid; k < nr; k += NTH) f.rows[nc + k] = ld2(f.scratch + k);
-        __syncthreads();
+    const int nr = nel - nc;   // every pick is eligible
+
+    // 6. the next wave's columns and rows, and the candidates' state
+#pragma unroll
+    for (int j = 0; j < kPre; ++j) {
+        if (j >= nblk) break;
+        const int k = j * NTH + tid;
+        if (k < r) {
+            int sl = slot[j];
+            if (sl >= TJ) sl = nc + (sl - TJ);
+            if (sl >= 0) {
+                f.rows[sl] = pv[j];
+                if (sl < nc) f.cols[sl] = pv[j];
+            }
+            f.crow[k] = sl;
+            f.cflag[k] = pfl[j];
+            f.part[k] = ppt[j];
+        }
+    }
+    for (int j = kPre; j < nblk; ++j) {
+        const int k = j * NTH + tid;
+        if (k >= r) continue;
+        int sl = ld2(f.scratch + k);
+        if (sl >= TJ) sl = nc + (sl - TJ);
+        if (sl >= 0) {
+            const int v = ld2(f.sigma + k);
+            f.rows[sl] = v;
+            if (sl < nc) f.cols[sl] = v;
+        }
+        f.crow[k] = sl;
     }
 
-    // 6. no live variable left: the root is the complete variable of lowest score (or
-    //    the forced one); the margin bound is the lowest other score (full if complete,
-    //    else a lower bound) minus the root's.  The candidates' scores are the ones
-    //    fetched for step 4 (step 4 changes flags only).
+    // 7. no live candidate left: the root is the complete variable of lowest score (or the
+    //    forced one); the margin bound is the lowest other score (full if complete, else a
+    //    lower bound) minus the root's; the sort keys of the next iteration's plan; and the
+    //    per-row coefficients 1/sqrt(1 - Sigma[w,root]^2) of UpdateData and UpdateCovMat,
+    //    computed here once for all rows in parallel.
     double second = INFINITY;
-    if (nc == 0) {
-        __shared__ double s_min[32];
-        for (int base = 0, j = 0; base < r; base += NTH, ++j) {
-            const int k = base + tid;
-            if (k >= r) break;
-            const int v = j < kPre ? pv[j] : ld2(f.sigma + k);
-            const double pt = j < kPre ? ppart[j] : ld2(f.part + v);
-            if (v != bv) second = fmin(second, pt);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) second = fmin(second, __shfl_xor_sync(0xffffffffu, second, o));
-        if ((tid & 31) == 0) s_min[tid >> 5] = second;
-        __syncthreads();
-        if (tid == 0)
-            for (int w = 0; w < NTH / 32; ++w) second = fmin(second, s_min[w]);
-    }
     int root = -1;
     if (nc == 0) {
-        // the iteration ends: its root, and the per-row coefficients 1/sqrt(1 - Sigma[w,root]^2)
-        // of UpdateData and UpdateCovMat, computed here once for all rows in parallel
         root = f.has_forced ? f.forced[it] : bv;
         const double* rootrow = f.sig + size_t(root) * p;
         const bool f32 = f.precision == LINGAM_MIXED;
-        for (int base = 0, j = 0; base < r; base += NTH, ++j) {
-            const int k = base + tid;
-            if (k >= r) break;
-            const int w = j < kPre ? pv[j] : ld2(f.sigma + k);
-            f.prev[w] = j < kPre ? ppart[j] : ld2(f.part + w);
+        auto end_one = [&](int w, double pt, int fl) {
+            if (w != bv && !(fl & kNoRoot) && okey(pt) < okey(second)) second = pt;
+            f.prev[w] = pt;
+            if (f.prior && f.prior[size_t(w) * p + root] == 1) f.anc_cnt[w] -= 1;   // root was a known ancestor
             if (w == root) {
+                s_rootpt = pt;
                 f.flags[w] = 0;
                 f.inv_root[w] = 0.0;
-                continue;
+                return;
             }
             const double c = rootrow[w];
             double om = fma(-c, c, 1.0);
@@ -636,7 +712,23 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
                 set_status(ctl, LINGAM_EDEGENERATE);
                 om = 1.0;
             }
-            f.inv_root[w] = 1.0 / sqrt(om);
+            f.inv_root[w] = rsqrt(om);
+        };
+#pragma unroll
+        for (int j = 0; j < kPre; ++j)
+            if (pv[j] >= 0) end_one(pv[j], ppt[j], pfl[j]);
+        for (int j = kPre; j < nblk; ++j) {
+            const int k = j * NTH + tid;
+            if (k < r) end_one(ld2(f.sigma + k), ld2(f.part + k), ld2(f.cflag + k));
+        }
+        long long ks = okey(second);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ks = min(ks, __shfl_xor_sync(0xffffffffu, ks, o));
+        if (lane == 0) s_col[wid] = __longlong_as_double(ks);
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 0; w < NW; ++w) ks = min(ks, okey(s_col[w]));
+            second = __longlong_as_double(ks);
         }
     }
     __syncthreads();   // every thread's writes precede the publication below
@@ -649,7 +741,7 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
             if (seq != 0) ctl->seq0 = seq;
             ctl->done = 1;
             f.order[it] = root;
-            f.rep_root_score[it] = root == bv ? best : ld2(f.part + root);
+            f.rep_root_score[it] = root == bv ? best : s_rootpt;
             f.rep_margin[it] = second - best;
             f.rep_pairs[it] = pairs0;
         } else {
@@ -687,6 +779,25 @@ __device__ __forceinline__ void acc2_add(Acc2& s, float2 u) {
     e.y = ex2_approx(-fabsf(y.y));
     s.P = __ffma2_rn(s.P, e, s.P);
     s.A = __fadd2_rn(s.A, make_float2(fabsf(y.x), fabsf(y.y)));
+}
+
+// I(x_i, x_j, r_i^(j), r_j^(i)) of Eq. Itest on the FP32 path, from a pair's merged sums
+// over the padded row: Ta, Tb the residuals' log-cosh sums centred by their variables'
+// group offsets (var_stats .w), Ga, Gb their sums of u' exp(-u^2/2) (u' = kScale u), and
+// the two variables' statistics si, sj.  Written as the difference of each residual's
+// entropy (Eq. HApp) from its own variable's,
+//   I = [H(r_i^(j)) - H(x_i)] - [H(r_j^(i)) - H(x_j)],
+// each bracket -k1 d (2 (m - beta) + d) - k2 (g_r - g)(g_r + g) with d = T / n + corr the
+// residual's mean log cosh minus its variable's, so that no FP32 term is larger than the
+// difference it contributes to.
+__device__ __forceinline__ float pair_measure_f(float Ta, float Ga, float Tb, float Gb, float4 si, float4 sj,
+                                                float inv_n) {
+    const float cg = kInvScale * inv_n;
+    const float da = fmaf(Ta, inv_n, si.x), db = fmaf(Tb, inv_n, sj.x);
+    const float ga = Ga * cg, gb = Gb * cg;
+    const float Da = -float(kK1) * da * (si.y + da) - float(kK2) * (ga - si.z) * (ga + si.z);
+    const float Db = -float(kK1) * db * (sj.y + db) - float(kK2) * (gb - sj.z) * (gb + sj.z);
+    return Da - Db;
 }
 
 // Shared state of one CTA (besides the dynamic copy ring).
@@ -801,25 +912,48 @@ __device__ __forceinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wav
         const int t = int(u / ng);
         const long long seg_end = min(g_hi, (long long)(t + 1) * ng);   // this CTA's groups of tile t
         T s_[4], sr_[4];
+        int vr[2], vc[2];   // this thread's two row and two column variables (-1: none)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = t * TI + rsl[h];
+            vr[h] = e < nrow ? ld2(f.rows + e) : -1;
+            vc[h] = csl[h] < ncol ? ld2(f.cols + csl[h]) : -1;
+        }
+        // FP32: the log-cosh group sums of a residual are centred by its variable's mean
+        // (var_stats), the row's for r_i^(j), the column's for r_j^(i)
+        float off_r[2], off_c[2];
+        if constexpr (kF32) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                off_r[h] = vr[h] >= 0 ? __ldcg(&f.vstat[vr[h]].w) : float(grp_off);
+                off_c[h] = vc[h] >= 0 ? __ldcg(&f.vstat[vc[h]].w) : float(grp_off);
+            }
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int e = t * TI + rsl[q >> 1], c = csl[q & 1];
-            const int vi = e < nrow ? ld2(f.rows + e) : -1;
-            const int vj = c < ncol ? ld2(f.cols + c) : -1;
+            const int vi = vr[q >> 1];
+            const int vj = vc[q & 1];
             bool okp = vi >= 0 && vj >= 0;
             if (okp) okp = f.reuse ? (e >= ncol || c < e) : (vi != vj);
-            double rho = okp ? f.sig[size_t(vi) * p + vj] : 0.0;
-            double om = fma(-rho, rho, 1.0);   // 1 - rho^2 in FP64
-            if (okp && !(om > degenerate_om(kF32))) {
-                set_status(ctl, LINGAM_EDEGENERATE);
-                om = 1.0;
-                rho = 0.0;
-            }
             if constexpr (kF32) {
-                const float sc = kScale / sqrtf(float(om));
+                // rho and 1 - rho^2 (formed in FP64, rounded once) from the FP32 companion of Sigma
+                float2 ro = okp ? __ldcg(f.sigf + size_t(vi) * p + vj) : make_float2(0.f, 1.f);
+                if (okp && !(ro.y > float(degenerate_om(true)))) {
+                    set_status(ctl, LINGAM_EDEGENERATE);
+                    ro = make_float2(0.f, 1.f);
+                }
+                const float sc = kScale / sqrtf(ro.y);
                 s_[q] = sc;
-                sr_[q] = sc * float(rho);
+                sr_[q] = sc * ro.x;
             } else {
+                double rho = okp ? f.sig[size_t(vi) * p + vj] : 0.0;
+                double om = fma(-rho, rho, 1.0);   // 1 - rho^2 in FP64
+                if (okp && !(om > degenerate_om(false))) {
+                    set_status(ctl, LINGAM_EDEGENERATE);
+                    om = 1.0;
+                    rho = 0.0;
+                }
                 const double sc = 1.0 / sqrt(om);
                 s_[q] = sc;
                 sr_[q] = sc * rho;
@@ -891,7 +1025,8 @@ __device__ __forceinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wav
                     for (int j = 0; j < 8; ++j) {
                         const float lsum = lg2_approx(acc[j].P.x * acc[j].P.y);
                         const float asum = acc[j].A.x + acc[j].A.y;
-                        D[j] += fmaf(float(kLn2), lsum, fmaf(asum, kInvScale / -kC3, grp_off));
+                        const float off = (j & 1) ? off_c[(j >> 1) & 1] : off_r[j >> 2];
+                        D[j] += fmaf(float(kLn2), lsum, fmaf(asum, kInvScale / -kC3, off));
                         Gt[j] += acc[j].G.x + acc[j].G.y;
                     }
                 }
@@ -1034,11 +1169,33 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
         const int e = t * TI + e_loc;
         const int vi = (tid < 256 && e < nrow) ? ld2(f.rows + e) : -1;
         const int vj = (tid < 256 && cc < ncol) ? ld2(f.cols + cc) : -1;
+        // FP32 path: the two variables' statistics, in flight while the slots are summed
+        float4 si = make_float4(0.f, 0.f, 0.f, 0.f), sj = si;
+        if constexpr (kF32) {
+            if (vi >= 0) si = __ldcg(f.vstat + vi);
+            if (vj >= 0) sj = __ldcg(f.vstat + vj);
+        }
         // 1. per warp: slots b_first + wid, + NW, ...; each lane 32 of the item's 1024 values
         T acc[32];
 #pragma unroll
         for (int k = 0; k < 32; ++k) acc[k] = T(0);
-        for (int bb = b_first + wid; bb <= b_last; bb += NW) {
+        int bb = b_first + wid;
+        if constexpr (kF32) {   // two slots' loads in flight; added in slot order
+            for (; bb + NW <= b_last; bb += 2 * NW) {
+                const T* src0 = parts + ((size_t(t) + bb) * CONS + part * 64) * 16 + lane * 32;
+                const T* src1 = src0 + size_t(NW) * CONS * 16;
+                T v0[32], v1[32];
+                load16_cg(v0, src0);
+                load16_cg(v0 + 16, src0 + 16);
+                load16_cg(v1, src1);
+                load16_cg(v1 + 16, src1 + 16);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) acc[k] += v0[k];
+#pragma unroll
+                for (int k = 0; k < 32; ++k) acc[k] += v1[k];
+            }
+        }
+        for (; bb <= b_last; bb += NW) {
             const T* src = parts + ((size_t(t) + bb) * CONS + part * 64) * 16 + lane * 32;
             T v[32];
             load16_cg(v, src);
@@ -1066,16 +1223,13 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
             T I = T(0);
             if (okp) {
                 if constexpr (kF32) {
-                    const float inv_n = float(1.0 / n);
-                    const float ha = hterm_f(tot[0] + float(pad_fix), tot[1] * kInvScale, inv_n);
-                    const float hb = hterm_f(tot[2] + float(pad_fix), tot[3] * kInvScale, inv_n);
-                    I = (float(f.hx[vj]) - float(f.hx[vi])) + (ha - hb);
+                    I = pair_measure_f(tot[0], tot[1], tot[2], tot[3], si, sj, __frcp_rn(float(f.n)));
                 } else {
                     const double ha = hterm(tot[0] + pad_fix, tot[1], n);
                     const double hb = hterm(tot[2] + pad_fix, tot[3], n);
                     I = (f.hx[vj] - f.hx[vi]) + (ha - hb);
                 }
-                if (!isfinite(double(I))) set_status(ctl, LINGAM_EDEGENERATE);
+                if (!isfinite(I)) set_status(ctl, LINGAM_EDEGENERATE);
             }
             // stage the item's I: its rows are complete (all TJ columns), local row index
             // = row within the item's first half, then the second half (TI / 2 further down)
@@ -1111,7 +1265,9 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
             if constexpr (kF32) {
                 FF acc;
                 for (int el = 0; el < IR; ++el) acc.add_sq(fmaxf(sI[el * (TJ + 1) + cc], 0.f));
-                cs = acc.value();
+                // the column part as a float-float pair in the slot's 8 bytes
+                const float2 ff = make_float2(acc.hi, acc.lo);
+                cs = *reinterpret_cast<const double*>(&ff);
             } else {
                 cs = 0.0;
                 for (int el = 0; el < IR; ++el) {
@@ -1121,9 +1277,13 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
             }
             f.colsum[(size_t(t) * PARTS + part) * TJ + cc] = cs;
         }
-        __threadfence();
+        // the barrier orders every thread's rowsum and colsum stores before thread 0's fence,
+        // whose release covers them for the CTA that counts the last item
         __syncthreads();
-        if (tid == 0) sh.flag = (atomicAdd(&ctl->merged, 1) == ntiles * PARTS - 1);
+        if (tid == 0) {
+            __threadfence();
+            sh.flag = (atomicAdd(&ctl->merged, 1) == ntiles * PARTS - 1);
+        }
         __syncthreads();
         if (sh.flag) {
             __threadfence();
@@ -1205,6 +1365,7 @@ __device__ __noinline__ void remove_data_phase(const Fit& f, IterShared& sh, int
                 Gs += sh.dred[16 + k2];
             }
             f.hx[w] = hterm(L, Gs, double(f.n));
+            f.vstat[w] = var_stats(L, Gs, f.n, f.ld);
         }
         __syncthreads();
     }
@@ -1245,8 +1406,9 @@ __device__ __noinline__ void remove_cov_phase(const Fit& f, int vb, int vG) {
             const int j = s_j[jj];
             if (w == root || j == root) continue;
             double* row = f.sig + size_t(w) * p;
-            if (j == w) row[j] = 1.0;
-            else row[j] = (row[j] - s_rj[kk] * s_rj[jj]) * (s_ij[kk] * s_ij[jj]);
+            const double nv = (j == w) ? 1.0 : (row[j] - s_rj[kk] * s_rj[jj]) * (s_ij[kk] * s_ij[jj]);
+            row[j] = nv;
+            if (f.precision == LINGAM_MIXED) f.sigf[size_t(w) * p + j] = sig_pair_f(nv);
         }
         __syncthreads();
         fence_proxy_async();   // the copy ring is written by bulk copies later
@@ -1258,10 +1420,116 @@ __device__ __noinline__ void remove_cov_phase(const Fit& f, int vb, int vG) {
             const int w = ld2(f.sigma + vb + m * vG);
             if (w == root || j == root || !(ld2(f.flags + j) & kAlive)) continue;
             double* row = f.sig + size_t(w) * p;
-            if (j == w) row[j] = 1.0;
-            else row[j] = (row[j] - rootrow[w] * rootrow[j]) * (ld2(f.inv_root + w) * ld2(f.inv_root + j));
+            const double nv =
+                (j == w) ? 1.0 : (row[j] - rootrow[w] * rootrow[j]) * (ld2(f.inv_root + w) * ld2(f.inv_root + j));
+            row[j] = nv;
+            if (f.precision == LINGAM_MIXED) f.sigf[size_t(w) * p + j] = sig_pair_f(nv);
         }
     }
+}
+
+// UpdateData and UpdateCovMat of one CTA's rows (k = vb, vb + vG, ... of the candidate
+// list) with the whole list staged in the idle copy ring first: every remaining variable's
+// index, Sigma[root, j] and 1/sqrt(1 - Sigma[root, j]^2), one pass for both updates.  The
+// rows stream one after another without a CTA barrier between them: each warp's sums of a
+// row go to shared memory and the new H(x_w) of all rows are formed after one barrier, in
+// the order of remove_data_phase (warp trees in the working precision, then the warps'
+// sums in FP64 in warp order), so the results are the same.
+template <class Cfg>
+__host__ __device__ constexpr size_t removal_stage_bytes(int r, int nmine) {
+    return size_t(r) * (sizeof(int) + 2 * sizeof(double)) + size_t(nmine) * 2 * (Cfg::CONS / 32) * sizeof(double);
+}
+
+template <class Cfg>
+__device__ __noinline__ void remove_staged(const Fit& f, int vb, int vG, int r, int root, int nmine) {
+    using T = typename Cfg::T;
+    constexpr int NTH = Cfg::CONS, NW = NTH / 32;
+    const int p = f.p, ld = f.ld, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const double* rootrow = f.sig + size_t(root) * p;
+    double* s_rj = reinterpret_cast<double*>(smem_dyn);
+    double* s_ij = s_rj + r;
+    double* s_hp = s_ij + r;   // [nmine][2 NW]: the warps' moment sums of each row
+    int* s_j = reinterpret_cast<int*>(s_hp + size_t(nmine) * 2 * NW);
+    for (int jj = tid; jj < r; jj += NTH) {
+        const int j = ld2(f.sigma + jj);
+        s_j[jj] = j;
+        s_rj[jj] = rootrow[j];
+        s_ij[jj] = ld2(f.inv_root + j);
+    }
+    __syncthreads();
+    // UpdateData (Algorithm 7) with the moments of the new rows
+    const T* xr = static_cast<const T*>(f.xt) + size_t(root) * ld;
+    for (int m = 0; m < nmine; ++m) {
+        const int k = vb + m * vG;
+        const int w = s_j[k];
+        if (w == root) continue;
+        const double c = s_rj[k], inv = s_ij[k];
+        T* xw = static_cast<T*>(f.xt) + size_t(w) * ld;
+        T lcc = T(0), g = T(0);
+        if constexpr (std::is_same<T, float>::value) {
+            const float cc = float(c), ii = float(inv);
+            float4* xw4 = reinterpret_cast<float4*>(xw);
+            const float4* xr4 = reinterpret_cast<const float4*>(xr);
+#pragma unroll 4
+            for (int t4 = tid; t4 < ld / 4; t4 += NTH) {
+                const float4 a = xw4[t4], rr = xr4[t4];
+                float4 o;
+                o.x = fmaf(-cc, rr.x, a.x) * ii;
+                o.y = fmaf(-cc, rr.y, a.y) * ii;
+                o.z = fmaf(-cc, rr.z, a.z) * ii;
+                o.w = fmaf(-cc, rr.w, a.w) * ii;
+                xw4[t4] = o;   // padding samples stay exactly zero
+                const int t = 4 * t4;
+                if (t + 0 < f.n) mom_add(o.x, lcc, g);
+                if (t + 1 < f.n) mom_add(o.y, lcc, g);
+                if (t + 2 < f.n) mom_add(o.z, lcc, g);
+                if (t + 3 < f.n) mom_add(o.w, lcc, g);
+            }
+        } else {
+            for (int t = tid; t < ld; t += NTH) {
+                const double u = fma(-c, xr[t], xw[t]) * inv;
+                xw[t] = u;
+                if (t < f.n) mom_add(u, lcc, g);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lcc += __shfl_xor_sync(0xffffffffu, lcc, o);
+            g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (lane == 0) {
+            s_hp[size_t(m) * 2 * NW + wid] = double(lcc);
+            s_hp[size_t(m) * 2 * NW + NW + wid] = double(g);
+        }
+    }
+    __syncthreads();
+    for (int m = tid; m < nmine; m += NTH) {
+        const int w = s_j[vb + m * vG];
+        if (w == root) continue;
+        double L = 0.0, Gs = 0.0;
+        for (int k2 = 0; k2 < NW; ++k2) {
+            L += s_hp[size_t(m) * 2 * NW + k2];
+            Gs += s_hp[size_t(m) * 2 * NW + NW + k2];
+        }
+        f.hx[w] = hterm(L, Gs, double(f.n));
+        f.vstat[w] = var_stats(L, Gs, f.n, f.ld);
+    }
+    // UpdateCovMat (Algorithm 8 / Eq. CovUpdate), FP64, one read-modify-write per element
+    const long long total = (long long)nmine * r;
+#pragma unroll 4
+    for (long long idx = tid; idx < total; idx += NTH) {
+        const int m = int(idx / r), jj = int(idx - (long long)m * r);
+        const int kk = vb + m * vG;
+        const int w = s_j[kk];
+        const int j = s_j[jj];
+        if (w == root || j == root) continue;
+        double* row = f.sig + size_t(w) * p;
+        const double nv = (j == w) ? 1.0 : (row[j] - s_rj[kk] * s_rj[jj]) * (s_ij[kk] * s_ij[jj]);
+        row[j] = nv;
+        if constexpr (std::is_same<T, float>::value) f.sigf[size_t(w) * p + j] = sig_pair_f(nv);
+    }
+    __syncthreads();
+    fence_proxy_async();   // the copy ring is written by bulk copies later
 }
 
 // ------------------------------------------------------------------ the iteration kernel
@@ -1278,8 +1546,16 @@ __device__ __noinline__ void iteration_tail(const Fit& f, int it, IterShared& sh
     if (int(blockIdx.x) == fc) {
         plan_phase<Cfg::CONS, Cfg::TI, Cfg::TJ>(f, it + 1, smem_dyn, sh.red, f.sigma_alt);
     } else {
-        remove_data_phase<Cfg>(f, sh, int(blockIdx.x), gridDim.x - 1);
-        remove_cov_phase<Cfg>(f, int(blockIdx.x), gridDim.x - 1);
+        volatile Ctl* vc = f.ctl;
+        const int r = vc->rm_r, root = vc->rm_root, vb = int(blockIdx.x), vG = int(gridDim.x) - 1;
+        if (r <= vb) return;   // no row of U for this CTA
+        const int nmine = (r - 1 - vb) / vG + 1;
+        if (removal_stage_bytes<Cfg>(r, nmine) <= ring_bytes<Cfg>()) {
+            remove_staged<Cfg>(f, vb, vG, r, root, nmine);
+        } else {
+            remove_data_phase<Cfg>(f, sh, vb, vG);
+            remove_cov_phase<Cfg>(f, vb, vG);
+        }
     }
 }
 
@@ -1589,9 +1865,7 @@ __device__ __noinline__ void batch_merge_warps(const Fit* fits, int count, Batch
             for (int k = 0; k < 32; ++k) acc[k] += vs[k];
         }
         // 2. I of the lane's 8 pairs, staged by (item row, column)
-        const double n = double(f.n);
-        const double pad_fix = double(f.ld - f.n) * kBeta;
-        const float inv_n = float(1.0 / n);
+        const float inv_n = __frcp_rn(float(f.n));
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int tp = 8 * lane + j;
@@ -1601,10 +1875,9 @@ __device__ __noinline__ void batch_merge_warps(const Fit* fits, int count, Batch
             if (okp) okp = f.reuse ? (e >= ncol || cc < e) : (vi[j] != vj[j]);
             float I = 0.f;
             if (okp) {
-                const float ha = hterm_f(acc[4 * j + 0] + float(pad_fix), acc[4 * j + 1] * kInvScale, inv_n);
-                const float hb = hterm_f(acc[4 * j + 2] + float(pad_fix), acc[4 * j + 3] * kInvScale, inv_n);
-                I = (float(f.hx[vj[j]]) - float(f.hx[vi[j]])) + (ha - hb);
-                if (!isfinite(double(I))) set_status(ctl, LINGAM_EDEGENERATE);
+                I = pair_measure_f(acc[4 * j + 0], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3],
+                                   __ldcg(f.vstat + vi[j]), __ldcg(f.vstat + vj[j]), inv_n);
+                if (!isfinite(I)) set_status(ctl, LINGAM_EDEGENERATE);
             }
             const int el = ct / HJ - part * (64 / HJ) + (q >> 1) * (64 / HJ);
             sI[el * (TJ + 1) + cc] = I;
@@ -1620,7 +1893,7 @@ __device__ __noinline__ void batch_merge_warps(const Fit* fits, int count, Batch
         if (lane < TJ) {
             FF a;
             for (int el = 0; el < IR; ++el) a.add_sq(fmaxf(sI[el * (TJ + 1) + lane], 0.f));
-            f.colsum[(size_t(t) * PARTS + part) * TJ + lane] = a.value();
+            reinterpret_cast<float2*>(f.colsum)[(size_t(t) * PARTS + part) * TJ + lane] = make_float2(a.hi, a.lo);
         }
         __threadfence();
         __syncwarp();
@@ -1739,7 +2012,10 @@ __device__ __noinline__ void batch_remove_data(const Fit* fits, int count, const
             L += __shfl_xor_sync(0xffffffffu, L, o);
             Gs += __shfl_xor_sync(0xffffffffu, Gs, o);
         }
-        if (lane == 0) f.hx[w] = hterm(L, Gs, double(n));
+        if (lane == 0) {
+            f.hx[w] = hterm(L, Gs, double(n));
+            f.vstat[w] = var_stats(L, Gs, n, ld);
+        }
     }
 }
 
@@ -1757,12 +2033,13 @@ __device__ __noinline__ void batch_remove_cov(const Fit* fits, int count, const 
         const int w = ld2(f.sigma + kk), j = ld2(f.sigma + jj);
         if (w == root || j == root) continue;
         double* row = f.sig + size_t(w) * p;
-        if (j == w) {
-            row[j] = 1.0;
-        } else {
+        double nv = 1.0;
+        if (j != w) {
             const double* rootrow = f.sig + size_t(root) * p;
-            row[j] = (row[j] - rootrow[w] * rootrow[j]) * (ld2(f.inv_root + w) * ld2(f.inv_root + j));
+            nv = (row[j] - rootrow[w] * rootrow[j]) * (ld2(f.inv_root + w) * ld2(f.inv_root + j));
         }
+        row[j] = nv;
+        if (f.precision == LINGAM_MIXED) f.sigf[size_t(w) * p + j] = sig_pair_f(nv);
     }
 }
 
@@ -1850,7 +2127,8 @@ static int grid_for(int nsm) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iteration<Cfg>, Cfg::CONS, smem) != cudaSuccess)
         return 0;
     if (per_sm < 1) return 0;
-    return nsm * (per_sm < Cfg::MINB ? per_sm : Cfg::MINB);   // all CTAs co-resident
+    const int grid = nsm * (per_sm < Cfg::MINB ? per_sm : Cfg::MINB);   // all CTAs co-resident
+    return grid < kMaxGrid ? grid : kMaxGrid;   // the workspace holds partial slots for kMaxGrid CTAs
 }
 
 int iteration_grid(const Fit& f, int nsm) {
@@ -1886,7 +2164,8 @@ static cudaError_t launch_batch_cfg(const Fit* fits_dev, int count, int maxp, Ct
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nsm * (per_sm < Cfg::MINB ? per_sm : Cfg::MINB));
+    const int grid = nsm * (per_sm < Cfg::MINB ? per_sm : Cfg::MINB);
+    cfg.gridDim = dim3(grid < kMaxGrid ? grid : kMaxGrid);   // partial slots exist for kMaxGrid CTAs
     cfg.blockDim = dim3(Cfg::CONS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;

@@ -56,6 +56,7 @@ __device__ void standardize_row(const Fit& f, const Tin* __restrict__ xr, const 
         f.mu[row] = mu;
         f.sd[row] = sd;
         f.hx[row] = hterm(L, G, double(n));
+        f.vstat[row] = var_stats(L, G, n, ld);
         f.flags[row] = kAlive;
     }
 }

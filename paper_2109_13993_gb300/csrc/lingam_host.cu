@@ -34,22 +34,22 @@ cudaError_t ensure_smem_attr(const void* func, size_t bytes) {
 }
 
 constexpr long long kMaxP = 16384;
-constexpr int kMaxGrid = 1024;   // pair-kernel CTAs at most (2 per SM)
 constexpr size_t kAlign = 256;
 
 static size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
     size_t total = 0;
-    size_t off_xin, off_xt, off_mu, off_sd, off_sig, off_sig0, off_hx, off_part, off_prev, off_flags, off_sigma, off_sigma_alt,
-        off_rows, off_cols, off_order, off_forced, off_scratch, off_rowsum, off_colsum, off_partials, off_invroot,
+    size_t off_xin, off_xt, off_mu, off_sd, off_sig, off_sig0, off_sigf, off_hx, off_vstat, off_part, off_cflag, off_crow, off_prev, off_flags,
+        off_sigma, off_sigma_alt,
+        off_rows, off_cols, off_order, off_forced, off_prior, off_anc, off_scratch, off_rowsum, off_colsum, off_partials, off_invroot,
         off_tilecnt, off_rs, off_rm, off_rp, off_rsc, off_cmat, off_rmat, off_rinv, off_bout, off_ctl, off_ibuf;
     int ld, maxtiles, maxsplit, esz;
 };
 
 static int chunk_of(int precision) { return precision == LINGAM_MIXED ? kChunk : kChunk64; }
 
-static Layout make_layout(long long p, long long n, int precision, int input_dtype) {
+static Layout make_layout(long long p, long long n, int precision, int input_dtype, bool with_prior = false) {
     Layout L;
     L.ld = int((n + kSampleAlign - 1) / kSampleAlign * kSampleAlign);
     L.esz = precision == LINGAM_MIXED ? 4 : 8;
@@ -73,16 +73,22 @@ static Layout make_layout(long long p, long long n, int precision, int input_dty
     L.off_sd = take(P * 8);
     L.off_sig = take(PP * 8);
     L.off_sig0 = take(PP * 8);
+    L.off_sigf = take(precision == LINGAM_MIXED ? PP * 8 : 0);
     L.off_hx = take(P * 8);
+    L.off_vstat = take(P * 16);
     L.off_part = take(P * 8);
+    L.off_cflag = take(P * 4);
+    L.off_crow = take(P * 4);
     L.off_prev = take(P * 8);
     L.off_flags = take(P * 4);
     L.off_sigma = take(P * 4);
     L.off_sigma_alt = take(P * 4);
-    L.off_rows = take((P + kTJ) * 4);   // the finalisation may write up to kTJ past the rows
+    L.off_rows = take(P * 4);
     L.off_cols = take(kTJ * 4);
     L.off_order = take(P * 4);
     L.off_forced = take(P * 4);
+    L.off_prior = take(with_prior ? PP : 0);
+    L.off_anc = take(with_prior ? P * 4 : 0);
     L.off_scratch = take(P * 4);
     L.off_rowsum = take(P * 8);
     L.off_colsum = take(size_t(L.maxtiles) * (kPairThreads / 64) * kTJ * 8);   // per (tile, merge item)
@@ -147,8 +153,12 @@ static Fit make_fit(char* base, const Layout& L, int p, int n, const lingam_opts
     f.sd = reinterpret_cast<double*>(base + L.off_sd);
     f.sig = reinterpret_cast<double*>(base + L.off_sig);
     f.sig0 = reinterpret_cast<double*>(base + L.off_sig0);
+    f.sigf = reinterpret_cast<float2*>(base + L.off_sigf);
     f.hx = reinterpret_cast<double*>(base + L.off_hx);
+    f.vstat = reinterpret_cast<float4*>(base + L.off_vstat);
     f.part = reinterpret_cast<double*>(base + L.off_part);
+    f.cflag = reinterpret_cast<int*>(base + L.off_cflag);
+    f.crow = reinterpret_cast<int*>(base + L.off_crow);
     f.prev = reinterpret_cast<double*>(base + L.off_prev);
     f.flags = reinterpret_cast<int*>(base + L.off_flags);
     f.sigma = reinterpret_cast<int*>(base + L.off_sigma);
@@ -180,17 +190,34 @@ static Fit make_fit(char* base, const Layout& L, int p, int n, const lingam_opts
     return f;
 }
 
+// Prior knowledge: values in {-1, 0, 1} and no cycle among the known ancestors (prior[i][j] = 1
+// is an edge j -> i); Kahn's algorithm over the p x p matrix.  Fills anc[i] = known ancestors
+// of variable i.
+static bool check_prior(const signed char* prior, int p, std::vector<int>& anc) {
+    anc.assign(size_t(p), 0);
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j < p; ++j) {
+            const signed char v = prior[size_t(i) * p + j];
+            if (v < -1 || v > 1) return false;
+            if (v == 1 && i != j) ++anc[size_t(i)];
+        }
+    std::vector<int> left(anc), queue;
+    for (int i = 0; i < p; ++i)
+        if (left[size_t(i)] == 0) queue.push_back(i);
+    for (size_t q = 0; q < queue.size(); ++q) {
+        const int j = queue[q];
+        for (int i = 0; i < p; ++i)
+            if (i != j && prior[size_t(i) * p + j] == 1 && --left[size_t(i)] == 0) queue.push_back(i);
+    }
+    return int(queue.size()) == p;
+}
+
 // cov_out != nullptr: stop after CalculateCovMat and copy Sigma (p x p) there.
 static int fit_one(const void* X, long long p_, long long n_, int* order, double* B, void* workspace,
                    const lingam_opts& o, lingam_report* rep, double* cov_out = nullptr) {
     if (!X || !(order || cov_out) || !workspace || p_ < 1 || n_ < 3 || p_ > kMaxP || n_ > (1ll << 30) || !valid_opts(o))
         return LINGAM_EINVAL;
-    if (!is_device_ptr(workspace) || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return LINGAM_EINVAL;
     const int p = int(p_), n = int(n_);
-    cudaStream_t st = static_cast<cudaStream_t>(o.stream);
-    const Layout L = make_layout(p_, n_, o.precision, o.input_dtype);
-    char* base = static_cast<char*>(workspace);
-
     if (o.forced_order) {   // must be a permutation of 0..p-1
         std::vector<char> seen(static_cast<size_t>(p), 0);
         for (int k = 0; k < p; ++k) {
@@ -199,6 +226,13 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
             seen[size_t(v)] = 1;
         }
     }
+    std::vector<int> anc;
+    const bool with_prior = o.prior != nullptr && !cov_out;
+    if (with_prior && !check_prior(o.prior, p, anc)) return LINGAM_EINVAL;
+    if (!is_device_ptr(workspace) || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return LINGAM_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(o.stream);
+    const Layout L = make_layout(p_, n_, o.precision, o.input_dtype, with_prior);
+    char* base = static_cast<char*>(workspace);
     int nsm = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return LINGAM_ECUDA;
@@ -206,6 +240,8 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
     Fit f = make_fit(base, L, p, n, o, rep && rep->scores);
     f.has_forced = o.forced_order != nullptr;
     f.forced = o.forced_order ? reinterpret_cast<const int*>(base + L.off_forced) : nullptr;
+    f.prior = with_prior ? reinterpret_cast<const signed char*>(base + L.off_prior) : nullptr;
+    f.anc_cnt = with_prior ? reinterpret_cast<int*>(base + L.off_anc) : nullptr;
     f.timing = o.timing ? 1 : 0;
 
 #define CK(call)                                  \
@@ -225,6 +261,10 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
     CK(cudaMemsetAsync(f.tile_cnt, 0, size_t(L.maxtiles) * 4, st));
     if (o.forced_order)
         CK(cudaMemcpyAsync(base + L.off_forced, o.forced_order, size_t(p) * 4, cudaMemcpyHostToDevice, st));
+    if (with_prior) {
+        CK(cudaMemcpyAsync(base + L.off_prior, o.prior, size_t(p) * p, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(base + L.off_anc, anc.data(), size_t(p) * 4, cudaMemcpyHostToDevice, st));
+    }
 
     const size_t in_bytes = size_t(p) * size_t(n) * (o.input_dtype == LINGAM_F32 ? 4 : 8);
     const void* xdev = X;
@@ -552,7 +592,7 @@ static int fit_many(std::vector<BatchItem>& items, void* workspace, const lingam
                     const BootSrc* boot) {
     const int count = int(items.size());
     if (count == 0) return LINGAM_OK;
-    if (!valid_opts(o) || o.forced_order || o.max_iters != 0 || !workspace) return LINGAM_EINVAL;
+    if (!valid_opts(o) || o.forced_order || o.prior || o.max_iters != 0 || !workspace) return LINGAM_EINVAL;
     if (!is_device_ptr(workspace) || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return LINGAM_EINVAL;
     std::vector<long long> P(static_cast<size_t>(count)), N(static_cast<size_t>(count));
     bool with_B = true, gather = true;
@@ -760,7 +800,7 @@ size_t lingam_workspace_size(long long p, long long n, const lingam_opts* opts) 
     lingam_default_opts(&o);
     if (opts) o = *opts;
     if (p < 1 || n < 3 || p > kMaxP || n > (1ll << 30) || !valid_opts(o)) return 0;
-    return make_layout(p, n, o.precision, o.input_dtype).total;
+    return make_layout(p, n, o.precision, o.input_dtype, o.prior != nullptr).total;
 }
 
 int lingam_fit(const void* X, long long p, long long n, int* order, double* B, void* workspace,

@@ -29,7 +29,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("input_dtype", ctypes.c_int), ("prune", ctypes.c_int),
                 ("reuse", ctypes.c_int), ("tile_i", ctypes.c_int), ("tile_j", ctypes.c_int),
                 ("split_n", ctypes.c_int), ("timeout_s", ctypes.c_double), ("stream", ctypes.c_void_p),
-                ("forced_order", _c_int_p), ("max_iters", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("forced_order", _c_int_p), ("max_iters", ctypes.c_int), ("timing", ctypes.c_int),
+                ("prior", ctypes.c_void_p)]
 
 
 class Report(ctypes.Structure):
@@ -119,7 +120,7 @@ def status_string(status: int) -> str:
 
 def make_opts(precision: str = "mixed", input_dtype=np.float32, prune: bool = True, reuse: bool = True,
               split_n: int = 0, timeout_s: float = 10.0, stream=None, forced_order=None, max_iters: int = 0,
-              timing: bool = False, tile_i: int = 0, tile_j: int = 0) -> tuple[Opts, object]:
+              timing: bool = False, tile_i: int = 0, tile_j: int = 0, prior=None) -> tuple[Opts, object]:
     o = Opts()
     load().lingam_default_opts(ctypes.byref(o))
     o.precision = {"mixed": LINGAM_MIXED, "fp64": LINGAM_FP64}[precision]
@@ -133,10 +134,15 @@ def make_opts(precision: str = "mixed", input_dtype=np.float32, prune: bool = Tr
     o.timing = int(bool(timing))
     o.tile_i = int(tile_i)
     o.tile_j = int(tile_j)
-    keep = None
+    keep = []
     if forced_order is not None:
-        keep = np.ascontiguousarray(forced_order, dtype=np.int32)
-        o.forced_order = keep.ctypes.data_as(_c_int_p)
+        fo = np.ascontiguousarray(forced_order, dtype=np.int32)
+        o.forced_order = fo.ctypes.data_as(_c_int_p)
+        keep.append(fo)
+    if prior is not None:
+        pr = np.ascontiguousarray(prior, dtype=np.int8)
+        o.prior = ctypes.c_void_p(pr.ctypes.data)
+        keep.append(pr)
     return o, keep
 
 
@@ -196,15 +202,16 @@ def _data_ptr(X):
 def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, forced_order=None,
         want_scores: bool = False, want_B: bool = True, split_n: int = 0, timeout_s: float = 10.0,
         stream=None, workspace=None, max_iters: int = 0, timing: bool = False, out=None,
-        tile_i: int = 0, tile_j: int = 0) -> FitResult:
-    """lingam_fit on X (p x n, numpy on the host or a torch tensor on the GPU)."""
+        tile_i: int = 0, tile_j: int = 0, prior=None) -> FitResult:
+    """lingam_fit on X (p x n, numpy on the host or a torch tensor on the GPU).  prior: None
+    or a p x p int8 array, prior[i, j] = 1 when X_j is a known ancestor of X_i."""
     L = load()
     ptr, p, n, dt, keep = _data_ptr(X)
     torch = _torch()
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     o, keep_forced = make_opts(precision, dt, prune, reuse, split_n, timeout_s, stream, forced_order, max_iters,
-                               timing, tile_i, tile_j)
+                               timing, tile_i, tile_j, prior)
     need = int(L.lingam_workspace_size(p, n, ctypes.byref(o)))
     if need == 0:
         raise LingamError(LINGAM_EINVAL, "invalid sizes or options")
@@ -313,18 +320,22 @@ def selftest_wait(which: int, timeout_s: float) -> int:
     return int(obs.value)
 
 
-def _reports(count, ps, want_report):
-    """Report structs with host arrays for root scores, margins and pair counts."""
-    if not want_report:
+def _reports(count, ps, want_report, want_scores=False):
+    """Report structs with host arrays for root scores, margins and pair counts (and the
+    p x p per-iteration score matrices when want_scores is set)."""
+    if not (want_report or want_scores):
         return None, None
     reps = (Report * count)()
     keep = []
     for k in range(count):
         rs, mg, pe = np.zeros(ps[k]), np.zeros(ps[k]), np.zeros(ps[k], dtype=np.int64)
+        sc = np.full((ps[k], ps[k]), np.nan) if want_scores else None
         reps[k].root_score = rs.ctypes.data_as(_c_dbl_p)
         reps[k].margin_lb = mg.ctypes.data_as(_c_dbl_p)
         reps[k].pairs_evaluated = pe.ctypes.data_as(_c_ll_p)
-        keep.append((rs, mg, pe))
+        if sc is not None:
+            reps[k].scores = sc.ctypes.data_as(_c_dbl_p)
+        keep.append((rs, mg, pe, sc))
     return reps, keep
 
 
@@ -337,6 +348,7 @@ class BatchResult:
     root_scores: list | None = None
     margins: list | None = None
     pairs: list | None = None
+    scores: list | None = None     # per dataset, p x p (want_scores): S_v at iteration k, NaN if not complete
 
 
 def batch_workspace(ps, ns, precision: str = "mixed", input_dtype=np.float32):
@@ -354,7 +366,7 @@ def batch_workspace(ps, ns, precision: str = "mixed", input_dtype=np.float32):
 
 
 def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = True, stream=None, workspace=None,
-              want_report: bool = False) -> BatchResult:
+              want_report: bool = False, want_scores: bool = False) -> BatchResult:
     """lingam_fit_batch over a list of datasets (numpy or torch, each p_k x n_k, one dtype)."""
     L = load()
     torch = _torch()
@@ -380,7 +392,7 @@ def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = T
     op = (ctypes.c_void_p * count)(*[o_.ctypes.data for o_ in orders])
     bp = (ctypes.c_void_p * count)(*[b.ctypes.data for b in Bs]) if Bs is not None else None
     status = np.zeros(count, dtype=np.int32)
-    reps, keep_rep = _reports(count, ps, want_report)
+    reps, keep_rep = _reports(count, ps, want_report, want_scores)
     st = L.lingam_fit_batch(count, xp, pa, na, op, bp, ctypes.c_void_p(workspace.data_ptr()), ctypes.byref(o),
                             status.ctypes.data_as(_c_int_p), reps)
     del items
@@ -389,11 +401,13 @@ def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = T
         res.root_scores = [k[0] for k in keep_rep]
         res.margins = [k[1] for k in keep_rep]
         res.pairs = [k[2] for k in keep_rep]
+        if want_scores:
+            res.scores = [k[3] for k in keep_rep]
     return res
 
 
 def fit_bootstrap(X, idx, precision: str = "mixed", prune: bool = True, want_B: bool = True, stream=None,
-                  workspace=None, want_report: bool = False) -> BatchResult:
+                  workspace=None, want_report: bool = False, want_scores: bool = False) -> BatchResult:
     """lingam_fit_bootstrap: X (p x n), idx (nboot x n column indices, numpy or CUDA tensor)."""
     L = load()
     torch = _torch()
@@ -417,7 +431,7 @@ def fit_bootstrap(X, idx, precision: str = "mixed", prune: bool = True, want_B: 
     order = np.zeros((nboot, p), dtype=np.int32)
     B = np.zeros((nboot, p, p)) if want_B else None
     status = np.zeros(nboot, dtype=np.int32)
-    reps, keep_rep = _reports(nboot, [p] * nboot, want_report)
+    reps, keep_rep = _reports(nboot, [p] * nboot, want_report, want_scores)
     st = L.lingam_fit_bootstrap(ctypes.c_void_p(ptr), p, n, nboot, ctypes.c_void_p(iptr), order.ctypes.data,
                                 B.ctypes.data if B is not None else None, ctypes.c_void_p(workspace.data_ptr()),
                                 ctypes.byref(o), status.ctypes.data_as(_c_int_p), reps)
@@ -427,6 +441,8 @@ def fit_bootstrap(X, idx, precision: str = "mixed", prune: bool = True, want_B: 
         res.root_scores = [k[0] for k in keep_rep]
         res.margins = [k[1] for k in keep_rep]
         res.pairs = [k[2] for k in keep_rep]
+        if want_scores:
+            res.scores = [k[3] for k in keep_rep]
     return res
 
 

@@ -153,6 +153,43 @@ def fig1_sem(n: int, seed: int) -> Dataset:
     return Dataset(X=X, B=B, order=order, noise_kind=np.zeros(5, dtype=np.int64))
 
 
+def scalability_dataset(p: int, n: int, dense: bool, seed: int) -> Dataset:
+    """The synthetic graphs of the paper's scalability experiment (Sec. V-D).
+
+    Every variable draws its number of parents uniformly from [1, 0.2 p] (sparse) or
+    [0.25 p, 0.5 p] (dense), capped by the number of variables before it in a random causal
+    order, and takes them uniformly among those; each edge weight is uniform in
+    [-0.95, -0.5] U [0.5, 0.95] (the paper prints the negative interval reversed); each
+    noise is Gaussian passed through sign(z)|z|^q with q uniform in [0.5, 0.8] U [1.2, 2].
+    Samples are generated recursively in causal order.  The paper does not say how it
+    keeps the variances finite (with 250-500 parents of weight up to 0.95 they overflow
+    within a few hundred variables); here every variable is scaled to unit sample variance
+    right after it is generated, which rescales its row of B and its noise and leaves the
+    causal structure as it is (B is returned for the scaled variables)."""
+    s_perm, s_cnt, s_par, s_w, s_q = (Stream(seed, t) for t in (21, 22, 23, 24, 25))
+    pi = s_perm.permutation(p)
+    lo, hi = (max(1, int(math.ceil(0.25 * p))), max(1, int(0.5 * p))) if dense else (1, max(1, int(0.2 * p)))
+    counts = s_cnt.integers(lo, hi, p)
+    B = np.zeros((p, p))
+    X = np.empty((p, n))
+    for k in range(p):
+        v = pi[k]
+        m = min(int(counts[k]), k)
+        z = Stream(seed, 3000 + v).normal(n)
+        u = s_q.uniform(2)
+        q = 0.5 + 0.3 * u[1] if u[0] < 0.5 else 1.2 + 0.8 * u[1]
+        x = np.sign(z) * np.abs(z) ** q
+        if m > 0:
+            par = pi[:k][np.argsort(s_par.uniform(k), kind="stable")[:m]]
+            w = (0.5 + 0.45 * s_w.uniform(m)) * np.where(s_w.uniform(m) < 0.5, -1.0, 1.0)
+            B[v, par] = w
+            x = x + w @ X[par]
+        sd = x.std(ddof=1)
+        X[v] = x / sd
+        B[v] /= sd
+    return Dataset(X=X, B=B, order=pi.astype(np.int64), noise_kind=np.full(p, NOISE_POWER))
+
+
 def bootstrap_indices(n: int, count: int, seed: int) -> np.ndarray:
     """count x n observation indices drawn with replacement (one row per resample)."""
     s = Stream(seed, 77)

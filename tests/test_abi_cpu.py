@@ -1,6 +1,7 @@
 """CPU checks of the C ABI library: it builds, loads, and exports every
 function include/lingam.h declares; the calls that need no GPU behave."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -121,3 +122,39 @@ def test_selftest_wait_rejects_bad_arguments_without_gpu_work(lib):
     assert lib.lingam_selftest_wait(0, 120.0, ctypes.byref(obs)) == lingam.LINGAM_EINVAL
     assert lib.lingam_selftest_wait(0, 0.05, None) == lingam.LINGAM_EINVAL
     assert obs.value == -7
+
+
+# The largest problems lingam_fit_static accepts, as stated in include/lingam.h (default
+# options; FP64 input on the FP64 path): (precision, n, largest p).
+STATIC_LIMITS = [("mixed", 10000, 128), ("mixed", 5000, 217), ("mixed", 1000, 430),
+                 ("fp64", 10000, 74), ("fp64", 5000, 136), ("fp64", 1000, 333)]
+
+
+@pytest.mark.parametrize("precision,n,pmax", STATIC_LIMITS)
+def test_static_scratch_limits_stated_in_the_header(lib, precision, n, pmax):
+    dt = np.float32 if precision == "mixed" else np.float64
+    assert 0 < lingam.workspace_size(pmax, n, precision, dt) <= lingam.STATIC_SCRATCH_BYTES
+    assert lingam.workspace_size(pmax + 1, n, precision, dt) > lingam.STATIC_SCRATCH_BYTES
+    hdr = open(os.path.join(build.INCLUDE, "lingam.h")).read()
+    assert f"p = {pmax} at\n" in hdr or f"p = {pmax} at " in hdr.replace("\n *     ", " ")
+
+
+def test_prior_knowledge_is_validated_without_gpu_work(lib):
+    # a cycle among the known ancestors, or a value outside -1..1, is rejected before any
+    # device work (the fit would otherwise fail on the host "workspace" with the same code,
+    # so the check is that the status is EINVAL for a valid workspace-free call too)
+    p, n = 6, 50
+    x = np.zeros((p, n), dtype=np.float32)
+    order = np.zeros(p, dtype=np.int32)
+    for bad in ("cycle", "value"):
+        prior = -np.ones((p, p), dtype=np.int8)
+        if bad == "cycle":
+            prior[1, 2] = prior[2, 4] = prior[4, 1] = 1
+        else:
+            prior[0, 3] = 5
+        o, keep = lingam.make_opts(prior=prior)
+        assert lib.lingam_fit(ctypes.c_void_p(x.ctypes.data), p, n, ctypes.c_void_p(order.ctypes.data), None,
+                              None, ctypes.byref(o), None) == lingam.LINGAM_EINVAL
+    # the workspace of a fit with prior knowledge holds the p x p matrix and the counts
+    o, keep = lingam.make_opts(prior=-np.ones((p, p), dtype=np.int8))
+    assert lib.lingam_workspace_size(100, 1000, ctypes.byref(o)) >= lingam.workspace_size(100, 1000) + 100 * 100

@@ -84,39 +84,86 @@ def test_batch_matches_single_fits():
             assert np.abs(B - single.B).max() <= 1e-6 * max(1.0, np.abs(single.B).max())
 
 
+def _member_vs_oracle(order, scores, root_score, margin_lb, o_order, o_S, atol, rtol=0.0):
+    """A batch member against the oracle, element by element.  The member and the oracle
+    start every iteration in the same state until their roots first differ (iteration k),
+    so at iterations 0..k every score the member completed is within atol + rtol |S| of the
+    oracle's, its root's score is the oracle's score of that root within the same bound,
+    and its margin lower bound does not exceed the oracle's margin by more than twice it.
+    The first difference must be an iteration whose oracle margin is within 2 tau (tau =
+    the largest error measured at that iteration, at least 2e-7 on the mixed path), so the
+    order is the oracle's whenever every margin is resolved.  Returns (k, max error)."""
+    p = len(o_order)
+    diff = np.nonzero(np.asarray(order) != np.asarray(o_order))[0]
+    k = int(diff[0]) if len(diff) else p
+    worst = 0.0
+    for it in range(min(k + 1, p)):
+        row, ora = scores[it], o_S[it]
+        complete = ~np.isnan(row)
+        assert not np.any(complete & np.isnan(ora)), f"iteration {it}: a removed variable has a score"
+        assert complete[order[it]], f"iteration {it}: the root's score is incomplete"
+        err = np.abs(row[complete] - ora[complete])
+        bound = atol + rtol * np.abs(ora[complete])
+        assert np.all(err <= bound), f"iteration {it}: max |dS| {err.max():.3e}"
+        assert abs(root_score[it] - ora[order[it]]) <= atol + rtol * abs(ora[order[it]])
+        worst = max(worst, float(err.max()))
+        alive = np.sort(ora[~np.isnan(ora)])
+        if len(alive) > 1:
+            tau = max(float(err.max()), 2e-7 if rtol == 0.0 else 1e-10 * alive[0])
+            true_margin = alive[1] - alive[0]
+            assert margin_lb[it] <= true_margin + 2 * (atol + rtol * alive[1])
+            if it == k:
+                assert true_margin <= 2 * tau, f"resolved iteration {it} differs"
+    return k, worst
+
+
+def _hard_members(rng_seed):
+    """A heavy-tailed member (one sample near the largest normalised value sqrt(n - 1)) and a
+    near-collinear member (1 - rho^2 = 2 x 2^-20 between two of its variables)."""
+    d = synth.lingam_dataset(10, 3000, 0.3, seed=rng_seed)
+    Xh = d.X.copy()
+    Xh[4, 10] += 1.0e4 * Xh[4].std()
+    d2 = synth.lingam_dataset(8, 3000, 0.3, seed=rng_seed + 1)
+    Xc = d2.X.copy()
+    e = synth.noise(synth.Stream(rng_seed, 5), synth.NOISE_UNIFORM, 3000)
+    Xc[7] = Xc[1] + np.sqrt(2.0 * 2.0 ** -20) * Xc[1].std() * e
+    return [Xh.astype(np.float32), Xc.astype(np.float32)]
+
+
 def test_batch_matches_oracle():
+    """Batch members (uneven sizes plus a heavy-tailed and a near-collinear member) against
+    the oracle: every complete score, root score and margin bound of every iteration on the
+    common prefix within 1e-4, and the full order wherever every margin is resolved."""
     sizes = [(5, 4000), (12, 3000), (20, 2000), (33, 2500)]
-    Xs, ds = [], []
+    ds = []
     for k, (p, n) in enumerate(sizes):
-        d = synth.lingam_dataset(p, n, min(1.0, 4.0 / (p - 1)), seed=40 + k)
-        ds.append(d.X.astype(np.float32))
-        Xs.append(_dev(ds[-1]))
-    res = lingam.fit_batch(Xs, precision="mixed", want_report=True)
+        ds.append(synth.lingam_dataset(p, n, min(1.0, 4.0 / (p - 1)), seed=40 + k).X.astype(np.float32))
+    ds += _hard_members(48)
+    res = lingam.fit_batch([_dev(X) for X in ds], precision="mixed", want_report=True, want_scores=True)
     assert res.status == 0
-    for X32, o, B in zip(ds, res.orders, res.Bs):
+    for m, (X32, o, B) in enumerate(zip(ds, res.orders, res.Bs)):
         o_order, o_B, o_S = oracle.fit(X32.astype(np.float64))
-        roots, margins = _oracle_margins(o_S)
-        k = _agree_until_unresolved(o, o_order, roots, margins)
-        print(f"p={X32.shape[0]}: batch order equals the oracle on {k} of {len(o)} iterations")
+        k, worst = _member_vs_oracle(o, res.scores[m], res.root_scores[m], res.margins[m], o_order, o_S, atol=1e-4)
+        print(f"member {m} (p={X32.shape[0]}): order equals the oracle on {k} of {len(o)} iterations, "
+              f"max |dS| {worst:.2e} on the common prefix")
         if k == len(o):
             assert np.abs(B - o_B).max() <= 1e-4 * max(1.0, np.abs(o_B).max())
 
 
 def test_batch_fp64_matches_oracle():
+    """FP64 batch members against the oracle: scores and root scores within 1e-10 relative
+    (floor 1e-14) on the common prefix, B within 1e-10 when the whole order agrees."""
     sizes = [(6, 2000), (15, 1500)]
     data = [synth.lingam_dataset(p, n, 0.4, seed=60 + k).X for k, (p, n) in enumerate(sizes)]
-    res = lingam.fit_batch([_dev(X, torch.float64) for X in data], precision="fp64")
+    res = lingam.fit_batch([_dev(X, torch.float64) for X in data], precision="fp64", want_report=True,
+                           want_scores=True)
     assert res.status == 0
-    for X, o, B in zip(data, res.orders, res.Bs):
+    for m, (X, o, B) in enumerate(zip(data, res.orders, res.Bs)):
         o_order, o_B, o_S = oracle.fit(X)
-        roots, margins = _oracle_margins(o_S)
-        # FP64 path: scores within 1e-10 relative, so every margin above 1e-9 resolves
-        for it in range(len(o) - 1):
-            if margins[it] > 1e-9 * max(1.0, roots[it]):
-                assert o[it] == o_order[it]
-            else:
-                break
-        else:
+        k, worst = _member_vs_oracle(o, res.scores[m], res.root_scores[m], res.margins[m], o_order, o_S,
+                                     atol=1e-14, rtol=1e-10)
+        print(f"FP64 member {m}: order equals the oracle on {k} of {len(o)} iterations, max |dS| {worst:.2e}")
+        if k == len(o):
             assert np.abs(B - o_B).max() <= 1e-10 * max(1.0, np.abs(o_B).max())
 
 
@@ -132,12 +179,15 @@ def test_bootstrap_matches_gathered_single_fits():
         single, roots, margins = _single(_dev(Xb))
         k = _agree_until_unresolved(res.orders[b], single.order, roots, margins)
         print(f"bootstrap {b}: order equals the gathered single fit on {k} of 20 iterations")
-    # two resamples against the oracle on the gathered data
+    # two resamples against the oracle on the gathered data, element by element
+    rs = lingam.fit_bootstrap(_dev(X), idx, precision="mixed", want_report=True, want_scores=True)
+    assert all(np.array_equal(a, b) for a, b in zip(res.orders, rs.orders))
     for b in (0, 5):
         Xb = X[:, idx[b]].astype(np.float64)
         o_order, o_B, o_S = oracle.fit(Xb)
-        roots, margins = _oracle_margins(o_S)
-        _agree_until_unresolved(res.orders[b], o_order, roots, margins)
+        k, worst = _member_vs_oracle(rs.orders[b], rs.scores[b], rs.root_scores[b], rs.margins[b], o_order, o_S,
+                                     atol=1e-4)
+        print(f"bootstrap {b} vs oracle: order equal on {k} of 20 iterations, max |dS| {worst:.2e}")
     # host indices and device indices give the same result; reports carry every
     # resample's evaluated pairs (at most all unordered pairs of each iteration)
     res2 = lingam.fit_bootstrap(_dev(X), torch.tensor(idx, device="cuda"), precision="mixed", want_report=True)

@@ -28,8 +28,8 @@ MUTANTS = {
                          "if ((st = oracle_regress(xj, xi, n, ri)) != ORACLE_OK) return st;"),
     "score_keeps_positive_part": ("double m = I < 0.0 ? I : 0.0;", "double m = I > 0.0 ? I : 0.0;"),
     "score_not_squared": ("s += m * m;", "s += -m;"),
-    "argmax_root": ("if (S[a] < S[best] || (S[a] == S[best] && U[a] < U[best])) best = a;",
-                    "if (S[a] > S[best] || (S[a] == S[best] && U[a] < U[best])) best = a;"),
+    "argmax_root": ("else if (S[a] < S[best] || (S[a] == S[best] && U[a] < U[best])) best = a;",
+                    "else if (S[a] > S[best] || (S[a] == S[best] && U[a] < U[best])) best = a;"),
     "no_centring_in_cov": ("for (long t = 0; t < n; ++t) s += (x[t] - mx) * (y[t] - my);",
                            "for (long t = 0; t < n; ++t) s += x[t] * y[t];"),
     "variance_divisor_n": ("v /= (double)(n - 1);", "v /= (double)n;"),
@@ -47,6 +47,9 @@ MUTANTS = {
     # a wrong partner set in FindRoot (Algorithm 2): the variable at position 0 of U is
     # never used as a partner
     "partner_set_drops_first": ("            if (b == a) continue;", "            if (b == a || b == 0) continue;"),
+    # prior knowledge read transposed (x_i taken as the known ancestor of x_j)
+    "prior_transposed": ("if (b != a && prior[(size_t)U[a] * p + U[b]] == 1) return 0;",
+                         "if (b != a && prior[(size_t)U[b] * p + U[a]] == 1) return 0;"),
     # RegressRoot (Algorithm 1) skips the first remaining variable
     "regress_root_skips_first": ("for (int a = 0; a < r && st == ORACLE_OK; ++a) {\n            int w = U[a];",
                                  "for (int a = 1; a < r && st == ORACLE_OK; ++a) {\n            int w = U[a];"),
