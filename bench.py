@@ -45,7 +45,7 @@ L2_FLUSH_BYTES = 256 << 20
 SFU_CLK_PER_PAIR_SAMPLE = 4.0 / 32.0 + (2.0 / 32.0) / 16.0
 # DRAM bytes (read + write) per launch of the iteration kernel, from an ncu capture of
 # the current kernel version (profiles/); None until the current version is captured.
-ITER_TRAFFIC_BYTES = None
+ITER_TRAFFIC_BYTES = 70.0e6   # ncu dram__bytes_read.sum + dram__bytes_write.sum, iteration 2 (55.9 + 14.1 MB)
 
 
 def unpruned_pair_samples(p: int, n: int) -> float:
@@ -260,10 +260,20 @@ def batched_workload(lingam, synth, torch, dev, stream, reps: int = 5) -> dict:
 
 
 def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else /proc/cpuinfo's model name or Arm part number."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    arm_parts = {"0xd4f": "Neoverse-V2", "0xd40": "Neoverse-V1", "0xd0c": "Neoverse-N1"}
     try:
         for line in open("/proc/cpuinfo"):
             if line.lower().startswith(("model name", "cpu part", "hardware")):
-                return line.split(":", 1)[1].strip()
+                v = line.split(":", 1)[1].strip()
+                return arm_parts.get(v, v)
     except OSError:
         pass
     return "unknown"
@@ -308,7 +318,18 @@ def configs_table(lingam, synth, torch, dev, stream, seeds=(1, 2, 3, 4, 5), reps
             row["fp64_ms" if not k else "fp64_first5_ms"], r64 = timed(
                 lambda: lingam.fit(X64, precision="fp64", workspace=ws64, max_iters=k))
             if dt_in == np.float32:
-                row["orders_agree"] = bool(np.array_equal((rm5 if k else rm).order[:k or p], r64.order[:k or p]))
+                om, o64 = (rm5 if k else rm).order[:k or p], r64.order[:k or p]
+                row["orders_agree"] = bool(np.array_equal(om, o64))
+                if not row["orders_agree"]:
+                    # where the two paths first part: the FP64 path's full scores at that
+                    # iteration (same history up to it) for the two roots picked
+                    it = int(np.argmax(om != o64))
+                    s64 = lingam.fit(X64, precision="fp64", workspace=ws64, prune=False, want_scores=True,
+                                     max_iters=it + 1).scores[it]
+                    a, b = s64[int(o64[it])], s64[int(om[it])]
+                    row["first_divergence"] = {"iteration": it, "fp64_score_fp64_root": float(a),
+                                               "fp64_score_mixed_root": float(b),
+                                               "relative_gap": float((b - a) / abs(a)) if a else None}
             rows.append(row)
             del ws64
         table[name] = rows
@@ -358,6 +379,62 @@ def scalability_sweep(lingam, synth, torch, dev, stream, reps: int = 3) -> list:
                              "pruned_fraction": 1.0 - r.pairs_total / r.pairs_unpruned})
                 del ws, X
     return rows
+
+
+def ablation(lingam, synth, torch, dev, stream, reps: int = 3) -> dict:
+    """The paper's two schedule claims measured on this GPU (Sec. III-A messaging, Sec. III-B
+    threshold): the p=300, n=5000 and p=1000, n=1e4 workloads (seed 1, mixed path) with the
+    threshold and the pair reuse on (the default), the threshold off, and both off; and the
+    sample-axis split (stream-K, the default) against one CTA per tile (split_n = 1), also on
+    a long-sample dataset (p=100, n=1e5); and the paper's own threshold schedule (gamma0
+    raised by factors c, Algorithms 6 and 9) in place of the running bound, with the number of
+    raises (each a kernel launch and read-back in the paper's host loop).  Full lingam_fit time
+    (median of `reps` after one untimed call) and pairs evaluated."""
+    out = {}
+    cases = [(name, synth.workload(name, seed=1)) for name in ("p300_n5000", "p1000_n10000")]
+    cases.append(("p100_n100000", synth.lingam_dataset(100, 100000, 4.0 / 99.0, seed=1)))
+    for name, d in cases:
+        X = torch.tensor(d.X.astype(np.float32), device=dev)
+        p, n = X.shape
+        ws = lingam.alloc_workspace(lingam.workspace_size(p, n), device=dev)
+        rows = {}
+        legs = [("threshold+messaging", dict()), ("split_n=1 (one CTA per tile)", dict(split_n=1))]
+        if name != "p100_n100000":
+            legs += [("messaging only", dict(prune=False)), ("neither", dict(prune=False, reuse=False))]
+            # the paper's schedule from a start below every root score of this fit, and from
+            # the median root score
+            r0 = lingam.fit(X, workspace=ws)
+            rs = r0.root_score[r0.root_score > 0]
+            lo, med = 1e-3 * float(rs.min()), float(np.median(rs))
+            legs += [(f"paper threshold gamma0={g0:.3g} c={c:g}", dict(gamma0=g0, gamma_c=c))
+                     for g0, c in ((lo, 2.0), (lo, 10.0), (med, 2.0))]
+        for label, kw in legs:
+            r = lingam.fit(X, workspace=ws, **kw)
+            ts = []
+            for _ in range(reps):
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lingam.fit(X, workspace=ws, **kw)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ts.append(e0.elapsed_time(e1))
+            rows[label] = {"fit_ms": float(np.median(ts)), "pair_evaluations": int(r.pairs_total), "_order": r.order}
+            if "gamma0" in kw:
+                rows[label]["threshold_updates"] = int(r.threshold_updates)
+        ref = rows["threshold+messaging"]["_order"]
+        for label, _ in legs:
+            rows[label]["order_equal_to_default"] = bool(np.array_equal(rows[label].pop("_order"), ref))
+        a = rows["threshold+messaging"]
+        rows["speedup_from_stream_k"] = rows["split_n=1 (one CTA per tile)"]["fit_ms"] / a["fit_ms"]
+        if "neither" in rows:
+            b, c = rows["messaging only"], rows["neither"]
+            rows["comparisons_saved_by_threshold"] = 1.0 - a["pair_evaluations"] / b["pair_evaluations"]
+            rows["speedup_from_threshold"] = b["fit_ms"] / a["fit_ms"]
+            rows["speedup_from_messaging"] = c["fit_ms"] / b["fit_ms"]
+        out[name] = rows
+        del ws
+    return out
 
 
 def run_ours(args, rank: int, world: int):
@@ -505,6 +582,8 @@ def run_ours(args, rank: int, world: int):
 
     if world == 1 and args.configs:
         line["configs"] = configs_table(lingam, synth, torch, dev, stream)
+    if world == 1 and args.ablation:
+        line["ablation"] = ablation(lingam, synth, torch, dev, stream)
     if world == 1 and args.sweep:
         line["scalability_sweep"] = scalability_sweep(lingam, synth, torch, dev, stream)
 
@@ -543,6 +622,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
     ap.add_argument("--max-iters", type=int, default=0, help="order only the first k iterations (profiling)")
+    ap.add_argument("--ablation", action="store_true",
+                    help="also time the threshold and the pair reuse switched off (the paper's schedule claims)")
     ap.add_argument("--sweep", action="store_true",
                     help="also run the paper's scalability grid (sparse/dense graphs, p x n)")
     ap.add_argument("--configs", action="store_true",

@@ -27,8 +27,11 @@
  *     pair-tile autotuner's table (lingam_autotune), the address of the
  *     static scratch area (lingam_fit_static), the executable graphs of batch
  *     calls (lingam_fit_batch, lingam_fit_bootstrap; keyed by workspace and
- *     shapes) and, per host thread and device, eight streams and their events
- *     for the independent per-problem launches of a batch.
+ *     shapes; at most 32 are kept, and capturing one more destroys the least
+ *     recently launched idle one) and, per host thread and device, the CUDA
+ *     events of the calls (created once, reused by every call) and eight
+ *     streams and their events for the independent per-problem launches of a
+ *     batch.
  *   - Data pointers may point to host or device memory; the library tells
  *     them apart with cudaPointerGetAttributes.  Host buffers are copied
  *     inside the call.  All device work is ordered on opts->stream (a batch
@@ -53,7 +56,9 @@ typedef enum {
                                  1 - rho^2 <= 2^-20 (mixed path) / 1e-14 (FP64 path): collinear */
     LINGAM_ENOMEM = -3,       /* reserved: the library itself never allocates */
     LINGAM_ECUDA = -4,        /* a CUDA runtime call or kernel launch failed */
-    LINGAM_ETIMEOUT = -5      /* a bounded device-side wait ran out (opts.timeout_s) */
+    LINGAM_ETIMEOUT = -5,     /* a bounded device-side wait ran out (opts.timeout_s) */
+    LINGAM_EBOUNDS = -6       /* debug build only (LINGAM_BOUNDS_CHECK): an index bound check of a
+                                 kernel failed; the access was skipped */
 } lingam_status;
 
 /* opts.precision */
@@ -69,7 +74,14 @@ typedef struct {
     int tile_i, tile_j;      /* pair-tile shape of the mixed path, rows x columns: 64 x 32, 32 x 32 or
                                 64 x 16 (a zero in one takes 64 rows or 32 columns); both 0 = the
                                 autotuner's table (lingam_tile_rows/_cols).  The FP64 path uses 32 x 32. */
-    int split_n;             /* sample-axis split override; 0 = autotuned */
+    int split_n;             /* single fits: split of the sample axis.  0 (default) = stream-K over
+                                (tile, 32-sample group) units: a wave's units are spread over the whole
+                                grid, so a tile's samples are cut into as many CTA segments as it takes
+                                to fill every SM.  s > 0 = at most ntiles * s CTAs work on a wave, so a
+                                tile is cut into about s segments (s = 1: one CTA per tile while a wave
+                                has fewer tiles than SMs).  Results move by FP32 rounding only (the
+                                partial moments of a tile are summed over its segments in fixed order).
+                                Ignored by the batch entry points. */
     double timeout_s;        /* bound on any device-side wait; <= 0 means 10 s */
     void* stream;            /* cudaStream_t to run on; NULL = the legacy default stream */
     const int* forced_order; /* NULL, or p variable indices (host memory): iteration k takes
@@ -89,6 +101,20 @@ typedef struct {
                                 the scores of the others are reported as NaN.  Values other than
                                 -1, 0, 1, or a cycle among the known ancestors: LINGAM_EINVAL.
                                 Single fits only (lingam_fit, lingam_fit_static, lingam_autotune). */
+    double gamma0;           /* 0 (default): threshold pruning against the lowest complete score of the
+                                iteration so far (exact, Sec. III-B).  > 0: the paper's own schedule
+                                instead (Sec. III-B, III-C; Algorithm 6 and the host loop of
+                                Algorithm 9), for ablation: each iteration starts with threshold
+                                gamma = gamma0; a variable whose partial score exceeds gamma stops
+                                taking new partners; when no variable is left to go on and none
+                                finished at or below gamma, gamma is multiplied by gamma_c until some
+                                variable can go on (or one that finished lies below it), and the
+                                stopped variables at or below the new gamma go on.  The root is
+                                the same as with gamma0 = 0 (both thresholds are exact); pairs
+                                evaluated and report.threshold_updates show the schedule's cost.
+                                Needs prune = reuse = 1; single fits only; NaN, negative or
+                                infinite: LINGAM_EINVAL. */
+    double gamma_c;          /* growth factor of gamma (> 1; default 2), used when gamma0 > 0 */
 } lingam_opts;
 
 typedef struct {
@@ -115,6 +141,9 @@ typedef struct {
        finalisation, up to the wave's published result), and of CTA 0's part of the
        removals (UpdateData, UpdateCovMat).  0 otherwise. */
     double t_compute_ms, t_merge_ms, t_remove_ms;
+    long long threshold_updates; /* opts.gamma0 > 0: times the threshold was multiplied by gamma_c,
+                                    summed over the iterations (each one a kernel launch and a
+                                    read-back in the paper's host loop, Algorithm 9); else 0 */
 } lingam_report;
 
 /* Fills *opts with the defaults: MIXED, F32, prune = reuse = 1, autotuned
@@ -187,16 +216,17 @@ int lingam_autotune(const void* X, long long p, long long n, void* workspace, co
 void lingam_autotune_reset(void);
 
 /*
- * lingam_selftest_wait -- failure detection check: one of the device-side waits of the
- * iteration kernel, made to wait for an event that never happens, must give up after
- * timeout_s seconds and record LINGAM_ETIMEOUT in its control block, and the kernel must
- * end normally (the context stays usable).  which = 0: an mbarrier phase that no thread
- * completes (the copy-ring waits); 1: the grid barrier with its arrival count started one
- * arrival off (two CTAs); 2: the wave word of a single fit that nothing publishes.  The
- * control block is a library-owned device variable.  *observed receives the recorded
- * status.  Returns LINGAM_EINVAL for which outside 0..2, timeout_s outside (0, 60] or a
- * NULL observed, LINGAM_ECUDA if the launch fails, else LINGAM_OK.  Synchronous on the
- * legacy default stream.
+ * lingam_selftest_wait -- failure detection check: one of the library's device-side waits,
+ * made to wait for an event that never happens, must give up after timeout_s seconds and
+ * record LINGAM_ETIMEOUT in its control block, and the kernel must end normally (the context
+ * stays usable).  which = 0: an mbarrier phase that no thread completes (the copy-ring waits
+ * of the iteration and batch kernels); 1: the grid barrier with its arrival count started one
+ * arrival off, two CTAs (the barrier of the iteration and batch kernels); 2: the wave word of
+ * a single fit that nothing publishes; 3: a row flag of the B fit's Cholesky that nothing
+ * sets.  The control block and flag are library-owned device variables.  *observed receives
+ * the recorded status.  Returns LINGAM_EINVAL for which outside 0..3, timeout_s outside
+ * (0, 60] or a NULL observed, LINGAM_ECUDA if the launch fails, else LINGAM_OK.  Synchronous
+ * on the legacy default stream.
  */
 int lingam_selftest_wait(int which, double timeout_s, int* observed);
 
@@ -218,8 +248,9 @@ size_t lingam_workspace_size_batch(int count, const long long* p, const long lon
  * over the whole GPU together.  The device work of a call is captured into a CUDA
  * graph on the second call with the same workspace and problem shapes (and options),
  * and replayed by every later such call; calls on the legacy default stream (NULL)
- * run without a graph.  opts->forced_order must be NULL and opts->max_iters 0; the
- * pair tiles are 32 x 32 on both paths.
+ * run without a graph.  opts->forced_order and opts->prior must be NULL, and
+ * opts->max_iters and opts->gamma0 0; opts->split_n is ignored; the pair tiles are
+ * 32 x 32 on both paths.
  */
 int lingam_fit_batch(int count, const void* const* X, const long long* p, const long long* n, int* const* order,
                      double* const* B, void* workspace, const lingam_opts* opts, int* status,

@@ -16,6 +16,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblingam_gb300.so")
+# the debug build: every kernel's index bound checks on (LINGAM_BOUNDS_CHECK, status LINGAM_EBOUNDS)
+DEBUG_BUILD = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(DEBUG_BUILD, "liblingam_gb300_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3",
          "-I" + INCLUDE, "-I" + CSRC]
@@ -38,7 +41,14 @@ def _headers_mtime() -> float:
     return max(os.path.getmtime(h) for h in hs)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, debug: bool = False) -> str:
+    """Compile the library (debug=True: the bound-checked variant, DEBUG_LIB) and return its path."""
+    if debug:
+        return _build_into(DEBUG_BUILD, DEBUG_LIB, force, verbose, ["-DLINGAM_BOUNDS_CHECK"] + list(extra or []))
+    return _build_into(BUILD, LIB, force, verbose, extra)
+
+
+def _build_into(BUILD: str, LIB: str, force: bool, verbose: bool, extra: list[str] | None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
     hdr = _headers_mtime()

@@ -81,6 +81,10 @@ struct Ctl {
     int rm_r, rm_root;
     unsigned seq0;
     int pad3;
+    // the paper's threshold schedule (Fit::gamma0 > 0): the current threshold, reset to gamma0
+    // at each iteration's plan, and the number of times it was raised over the fit
+    double gamma;
+    long long gsteps;
 };
 
 __host__ __device__ inline unsigned long long pack_wave(unsigned seq, int done, int ntiles, int ncol, int nrow) {
@@ -158,10 +162,25 @@ struct Fit {
     int tile_rows;       // rows of a pair tile: 64 or 32 (mixed path), 32 (FP64 path)
     int tile_cols;       // columns of a pair tile (= of a wave): 32, or 16 (mixed path)
     int maxsplit;        // sample splits at most
+    int nslots;          // partial-moment slots (one per tile and CTA segment of a wave) the workspace holds
+    int split_n;         // single fits: at most about split_n CTAs share a tile's samples (0 = as many as fill the grid)
+    double gamma0;       // 0: prune against the lowest complete score; > 0: the paper's threshold
+                         // schedule (Sec. III-B/C): threshold gamma0, times gamma_c while no variable
+                         // can finish below it
+    double gamma_c;
 };
 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_status(Ctl* ctl, int code) { atomicCAS(&ctl->status, 0, code); }
+
+// Index bound checks of the debug build (compiled with -DLINGAM_BOUNDS_CHECK): a failed check
+// records LINGAM_EBOUNDS in the control block and the guarded access is skipped.  In the
+// release build the checks are constant true and cost nothing.
+#ifdef LINGAM_BOUNDS_CHECK
+#define LINGAM_INBOUNDS(ctl, cond) ((cond) ? true : (set_status((ctl), LINGAM_EBOUNDS), false))
+#else
+#define LINGAM_INBOUNDS(ctl, cond) true
+#endif
 
 // The FP32 pair kernel's view of a covariance element (Fit::sigf).
 __device__ __forceinline__ float2 sig_pair_f(double rho) { return make_float2(float(rho), float(fma(-rho, rho, 1.0))); }
@@ -170,6 +189,23 @@ __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// Bounded wait until *flag becomes nonzero (the B fit's per-row readiness flags): false, with
+// LINGAM_ETIMEOUT recorded in ctl, when it did not within ctl's timeout.
+__device__ inline bool wait_flag_set(const volatile int* flag, Ctl* ctl) {
+    unsigned long long t0 = 0, tmo = 0;
+    while (*flag == 0) {
+        const unsigned long long now = global_ns();
+        if (t0 == 0) {
+            t0 = now;
+            tmo = *reinterpret_cast<volatile unsigned long long*>(&ctl->timeout_ns);
+        } else if (now - t0 > tmo) {
+            set_status(ctl, LINGAM_ETIMEOUT);
+            return false;
+        }
+    }
+    return true;
 }
 
 // MUFU base-2 exponential and logarithm (flush-to-zero approximations).

@@ -104,19 +104,7 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_coop(Fit f) {
         if (tid == 0) {
             int ok = 1;
             if (k > 0) {
-                volatile int* rk_flag = ready + k;
-                unsigned long long t0 = 0, tmo = 0;
-                while (*rk_flag == 0) {
-                    const unsigned long long now = global_ns();
-                    if (t0 == 0) {
-                        t0 = now;
-                        tmo = *reinterpret_cast<volatile unsigned long long*>(&f.ctl->timeout_ns);
-                    } else if (now - t0 > tmo) {
-                        set_status(f.ctl, LINGAM_ETIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                }
+                ok = wait_flag_set(ready + k, f.ctl) ? 1 : 0;
                 __threadfence();
             }
             s_ok = ok;

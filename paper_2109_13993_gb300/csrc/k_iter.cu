@@ -309,7 +309,7 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
         const int a = (v < p) ? (ld2(f.flags + v) & kAlive) : 0;
         int tot;
         const int rank = r + scan01<NTH>(a ? 1 : 0, red, &tot);
-        if (a) sigma[rank] = v;
+        if (a && LINGAM_INBOUNDS(ctl, rank < p)) sigma[rank] = v;
         r += tot;
         __syncthreads();
     }
@@ -385,7 +385,7 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
                 const int c = v >= 0 && ((ld2(f.anc_cnt + v) == 0) == (pass == 0));
                 int tot;
                 const int rank = out + scan01<NTH>(c, red, &tot);
-                if (c) sigma[rank] = v;
+                if (c && LINGAM_INBOUNDS(ctl, rank < p)) sigma[rank] = v;
                 out += tot;
                 __syncthreads();
             }
@@ -410,6 +410,7 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
         ctl->best = INFINITY;
         ctl->best_var = -1;
         ctl->pairs_it = 0;
+        ctl->gamma = f.gamma0;
         if (r <= 1) {
             // Algorithm 2: a single remaining variable is the root
             const int root = r == 1 ? sigma[0] : -1;
@@ -467,7 +468,7 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
     const int nblk = (r + NTH - 1) / NTH;
     __shared__ double s_col[32 * 33];
     __shared__ double s_tot[32];
-    __shared__ double s_best, s_rootpt;
+    __shared__ double s_best, s_rootpt, s_gamma;
     __shared__ int s_bestv;
     __shared__ double s_csc[32];   // the wave's complete scores, by column
     __shared__ int s_cv[32];       // and their variables
@@ -513,13 +514,14 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
             }
         }
     }
-    double best0 = INFINITY;
+    double best0 = INFINITY, gamma0 = 0.0;
     int bv0 = -1;
     long long pairs0 = 0;
     if (tid == 0) {
         best0 = vc->best;
         bv0 = vc->best_var;
         pairs0 = vc->pairs_it;
+        gamma0 = vc->gamma;
     }
     // 2. the row contribution min(0, I(row, col))^2 summed over the wave's columns, of every
     //    candidate that is a row of this wave (by its row slot)
@@ -603,11 +605,15 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
             ctl->pairs_it = pairs0;
             s_best = best0;
             s_bestv = bv0;
+            s_gamma = gamma0;
         }
     }
     __syncthreads();
     const double best = s_best;
     const int bv = s_bestv;
+    // the paper's threshold schedule (gamma0 > 0) in place of the running bound
+    const bool gmode = f.gamma0 > 0.0 && f.prune && reuse;
+    double thr = s_gamma;
 
     // 5. prune (partial score above the threshold), pick the next columns (the first TJ live
     //    un-columned candidates in candidate order) and rank the next rows (every other
@@ -629,31 +635,72 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
         const bool col = (fl & kColumned) != 0;
         live = 0;
         if (!col) {
-            if (!(fl & kDead) && f.prune && reuse && okey(pt) > okey(best)) fl |= kDead;
+            if (gmode) {   // stopped while above the current threshold; goes on once it is not
+                fl = okey(pt) > okey(thr) ? (fl | kDead) : (fl & ~kDead);
+            } else if (!(fl & kDead) && f.prune && reuse && okey(pt) > okey(best)) {
+                fl |= kDead;
+            }
             live = (fl & (kDead | kNoRoot)) ? 0 : 1;
         }
         elig = reuse ? !col : 1;
     };
+    int nc = 0, nr = 0;
+    for (int pass = 0;; ++pass) {
+        nlive = nel = 0;
 #pragma unroll
-    for (int j = 0; j < kPre; ++j) {
-        if (j >= nblk) break;
-        int live = 0, elig = 0;
-        if (pv[j] >= 0) prune_one(pfl[j], ppt[j], live, elig);
-        rank_one(live, elig, slot[j]);
-    }
-    for (int j = kPre; j < nblk; ++j) {
-        const int k = j * NTH + tid;
-        int live = 0, elig = 0, sl = -1;
-        if (k < r) {
-            int fl = ld2(f.cflag + k);
-            prune_one(fl, ld2(f.part + k), live, elig);
-            f.cflag[k] = fl;
+        for (int j = 0; j < kPre; ++j) {
+            if (j >= nblk) break;
+            int live = 0, elig = 0;
+            if (pv[j] >= 0) prune_one(pfl[j], ppt[j], live, elig);
+            rank_one(live, elig, slot[j]);
         }
-        rank_one(live, elig, sl);
-        if (k < r) f.scratch[k] = sl;
+        for (int j = kPre; j < nblk; ++j) {
+            const int k = j * NTH + tid;
+            int live = 0, elig = 0, sl = -1;
+            if (k < r) {
+                int fl = ld2(f.cflag + k);
+                prune_one(fl, ld2(f.part + k), live, elig);
+                f.cflag[k] = fl;
+            }
+            rank_one(live, elig, sl);
+            if (k < r) f.scratch[k] = sl;
+        }
+        nc = nlive < TJ ? nlive : TJ;
+        nr = nel - nc;   // every pick is eligible
+        // The paper's schedule: nothing can go on and nothing finished at or below gamma (the
+        // iteration cannot end yet): raise gamma by factors gamma_c until the lowest partial
+        // score of a variable that may still be the root, or the lowest complete score, is at
+        // or below it, and rank once more.  One raise suffices for the second pass.
+        if (!gmode || nc > 0 || okey(best) <= okey(thr) || pass > 0) break;
+        long long km = okey(best);
+#pragma unroll
+        for (int j = 0; j < kPre; ++j)
+            if (pv[j] >= 0 && !(pfl[j] & (kColumned | kNoRoot))) km = min(km, okey(ppt[j]));
+        for (int j = kPre; j < nblk; ++j) {
+            const int k = j * NTH + tid;
+            if (k < r && !(ld2(f.cflag + k) & (kColumned | kNoRoot))) km = min(km, okey(ld2(f.part + k)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) km = min(km, __shfl_xor_sync(0xffffffffu, km, o));
+        if (lane == 0) s_col[wid] = __longlong_as_double(km);
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 0; w < NW; ++w) km = min(km, okey(s_col[w]));
+            const double target = __longlong_as_double(km);
+            double g = thr;
+            long long k = 0;
+            while (g < target && k < 4096) {   // gamma_c > 1 and target finite: a few steps
+                g *= f.gamma_c;
+                ++k;
+            }
+            if (!(g >= target)) g = target;
+            s_gamma = g;
+            ctl->gamma = g;
+            ctl->gsteps += k;
+        }
+        __syncthreads();
+        thr = s_gamma;
     }
-    const int nc = nlive < TJ ? nlive : TJ;
-    const int nr = nel - nc;   // every pick is eligible
 
     // 6. the next wave's columns and rows, and the candidates' state
 #pragma unroll
@@ -663,7 +710,7 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
         if (k < r) {
             int sl = slot[j];
             if (sl >= TJ) sl = nc + (sl - TJ);
-            if (sl >= 0) {
+            if (sl >= 0 && LINGAM_INBOUNDS(ctl, sl < p && (sl >= nc || sl < kTJ))) {
                 f.rows[sl] = pv[j];
                 if (sl < nc) f.cols[sl] = pv[j];
             }
@@ -677,7 +724,7 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
         if (k >= r) continue;
         int sl = ld2(f.scratch + k);
         if (sl >= TJ) sl = nc + (sl - TJ);
-        if (sl >= 0) {
+        if (sl >= 0 && LINGAM_INBOUNDS(ctl, sl < p && (sl >= nc || sl < kTJ))) {
             const int v = ld2(f.sigma + k);
             f.rows[sl] = v;
             if (sl < nc) f.cols[sl] = v;
@@ -841,7 +888,7 @@ __device__ __forceinline__ void issue_part(const Fit& f, typename Cfg::T* stage,
         cvar = v;
     }
     if (threadIdx.x == 0) mbar_expect_tx(bar, uint32_t(TI + TJ) * CH * sizeof(T));
-    if (lane < SPW) {
+    if (lane < SPW && LINGAM_INBOUNDS(f.ctl, cvar < f.p && size_t(c + 1) * CH <= size_t(f.ld))) {
         fence_proxy_async();
         const T* xt = static_cast<const T*>(f.xt);
         bulk_g2s(stage + slot * LDS, xt + size_t(cvar >= 0 ? cvar : 0) * f.ld + size_t(c) * CH, CH * sizeof(T), bar);
@@ -1119,6 +1166,7 @@ __device__ __forceinline__ bool compute_phase(const Fit& f, Ctl* gctl, const Wav
         }
         // this CTA's partial moments of tile t: slot t + bs
         T* dst = parts + ((size_t(t) + bs) * CONS + tid) * 16;
+        if (LINGAM_INBOUNDS(ctl, t + bs < f.nslots))
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             dst[4 * q + 0] = D[2 * q];
@@ -1180,6 +1228,7 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
 #pragma unroll
         for (int k = 0; k < 32; ++k) acc[k] = T(0);
         int bb = b_first + wid;
+        if (!LINGAM_INBOUNDS(ctl, t + b_last < f.nslots)) bb = b_last + 1;   // no slot read
         if constexpr (kF32) {   // two slots' loads in flight; added in slot order
             for (; bb + NW <= b_last; bb += 2 * NW) {
                 const T* src0 = parts + ((size_t(t) + bb) * CONS + part * 64) * 16 + lane * 32;
@@ -1258,7 +1307,7 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
                     rs = fma(m, m, rs);
                 }
             }
-            if (e < nrow) f.rowsum[e] = rs;
+            if (e < nrow && LINGAM_INBOUNDS(ctl, e < f.p)) f.rowsum[e] = rs;
         } else if (tid >= 32 && tid < 32 + TJ) {
             const int cc = tid - 32;
             double cs;
@@ -1644,7 +1693,11 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
     bool done = vc->done != 0;
     // wave words are numbered on from the last wave of the previous iteration
     for (unsigned seq = *reinterpret_cast<volatile unsigned*>(&ctl->seq0) + 1; !done; ++seq) {
-        const Span sp = single_span((long long)wv.ntiles * (f.ld / kSub), gridDim.x);
+        // opts.split_n caps the CTAs of the wave at split_n per tile (split_n = 1: each tile on
+        // one CTA where the wave has fewer tiles than the grid has CTAs); 0 = the whole grid
+        const long long gcap = f.split_n > 0 ? min((long long)gridDim.x, (long long)wv.ntiles * f.split_n)
+                                             : (long long)gridDim.x;
+        const Span sp = single_span((long long)wv.ntiles * (f.ld / kSub), gcap);
         if (!compute_phase<Cfg>(f, ctl, wv, sp, ring, full, empty, sh, chunk_base)) {
             ctl->abort = 1;
             return;
@@ -1841,19 +1894,20 @@ __device__ __noinline__ void batch_merge_warps(const Fit* fits, int count, Batch
         }
         // 1. the item's 1024 values, 32 per lane, over its slots
         const float* parts = static_cast<const float*>(f.partials);
+        const int b_stop = LINGAM_INBOUNDS(ctl, t + b_last < f.nslots) ? b_last : b_first - 1;
         float acc[32];
 #pragma unroll
         for (int k = 0; k < 32; ++k) acc[k] = 0.f;
         for (int w = 0; w < NW; ++w) {
             int bb = b_first + w;
-            if (bb > b_last) continue;   // an empty virtual warp adds +0: no change
+            if (bb > b_stop) continue;   // an empty virtual warp adds +0: no change
             float vs[32];
             {
                 const float* src = parts + ((size_t(t) + bb) * CONS + part * 64) * 16 + lane * 32;
                 load16_cg(vs, src);
                 load16_cg(vs + 16, src + 16);
             }
-            for (bb += NW; bb <= b_last; bb += NW) {
+            for (bb += NW; bb <= b_stop; bb += NW) {
                 const float* src = parts + ((size_t(t) + bb) * CONS + part * 64) * 16 + lane * 32;
                 float v[32];
                 load16_cg(v, src);
@@ -2185,13 +2239,16 @@ cudaError_t launch_batch(const Fit* fits_dev, int count, int maxp, int precision
 }
 
 // ------------------------------------------------------------------ bounded-wait self-test
-// Each of the iteration kernel's three kinds of wait, made to wait for something that never
+// Each kind of device-side wait of the library, made to wait for something that never
 // happens, must give up after the control block's timeout with LINGAM_ETIMEOUT recorded and
 // let the kernel end normally: which = 0, an mbarrier phase that no thread completes (the
-// copy-ring waits); 1, a grid barrier whose arrival count starts one off, so that the second
-// of two CTAs waits for an arrival that never comes; 2, a wave word that nothing publishes.
+// copy-ring waits of the iteration and batch kernels); 1, a grid barrier whose arrival count
+// starts one off, so that the second of two CTAs waits for an arrival that never comes (the
+// iteration and batch kernels' barriers); 2, a wave word that nothing publishes; 3, a B-fit
+// row flag that nothing sets (the Cholesky's data flow).
 // No copies or tensor-memory allocations are in flight in this kernel.
 __device__ Ctl g_selftest_ctl;
+__device__ int g_selftest_flag;   // stays 0: the readiness flag nothing sets
 
 __global__ void k_wait_selftest(int which) {
     __shared__ __align__(8) uint64_t bar;
@@ -2208,6 +2265,8 @@ __global__ void k_wait_selftest(int which) {
         mbar_wait_or_abort(&bar, 0, ctl, tmo, &s_abort);
     } else if (which == 1) {
         grid_sync(ctl, tmo);
+    } else if (which == 3) {
+        if (threadIdx.x == 0) wait_flag_set(&g_selftest_flag, ctl);
     } else {
         Wave wv;
         bool done = false;
@@ -2219,6 +2278,9 @@ cudaError_t run_wait_selftest(int which, unsigned long long timeout_ns, int* sta
     Ctl h = {};
     h.timeout_ns = timeout_ns;
     if (which == 1) h.bar_count = 1;   // one arrival off: the second CTA's block never fills
+    const int zero = 0;
+    cudaError_t ez = cudaMemcpyToSymbolAsync(g_selftest_flag, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
+    if (ez != cudaSuccess) return ez;
     cudaError_t e = cudaMemcpyToSymbolAsync(g_selftest_ctl, &h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     k_wait_selftest<<<which == 1 ? 2 : 1, 32, 0, st>>>(which);

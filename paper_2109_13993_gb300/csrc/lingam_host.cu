@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -38,13 +40,32 @@ constexpr size_t kAlign = 256;
 
 static size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// Host-side fault injection for tests of the error paths (no GPU fault is involved):
+// the environment variable LINGAM_FAULT names a step of a call -- "standardize",
+// "covariance", "iteration" (optionally "iteration:<k>" for iteration k), "bfit" or "batch"
+// -- and that step reports a failed launch (LINGAM_ECUDA) instead of launching.
+static bool inject_fault(const char* step, int k = -1) {
+    const char* e = std::getenv("LINGAM_FAULT");
+    if (!e || !*e) return false;
+    const size_t n = std::strlen(step);
+    if (std::strncmp(e, step, n) != 0) return false;
+    if (e[n] == '\0') return true;
+    return e[n] == ':' && k >= 0 && std::atoi(e + n + 1) == k;
+}
+
+// LINGAM_LOG >= 1: one line per call on stderr (sizes, status, launches, device times).
+static int log_level() {
+    const char* e = std::getenv("LINGAM_LOG");
+    return e ? std::atoi(e) : 0;
+}
+
 struct Layout {
     size_t total = 0;
     size_t off_xin, off_xt, off_mu, off_sd, off_sig, off_sig0, off_sigf, off_hx, off_vstat, off_part, off_cflag, off_crow, off_prev, off_flags,
         off_sigma, off_sigma_alt,
         off_rows, off_cols, off_order, off_forced, off_prior, off_anc, off_scratch, off_rowsum, off_colsum, off_partials, off_invroot,
         off_tilecnt, off_rs, off_rm, off_rp, off_rsc, off_cmat, off_rmat, off_rinv, off_bout, off_ctl, off_ibuf;
-    int ld, maxtiles, maxsplit, esz;
+    int ld, maxtiles, maxsplit, esz, nslots;
 };
 
 static int chunk_of(int precision) { return precision == LINGAM_MIXED ? kChunk : kChunk64; }
@@ -96,7 +117,8 @@ static Layout make_layout(long long p, long long n, int precision, int input_dty
     // uses more CTAs than it has (tile, 32-sample group) units
     const size_t units = size_t(L.maxtiles) * size_t(L.ld / kSub);
     // (the Gram's split partial tiles use the same region before the first iteration)
-    const size_t pair_partials = (size_t(L.maxtiles) + std::min(size_t(kMaxGrid), units)) * kPairThreads * 16 * L.esz;
+    L.nslots = int(size_t(L.maxtiles) + std::min(size_t(kMaxGrid), units));
+    const size_t pair_partials = size_t(L.nslots) * kPairThreads * 16 * L.esz;
     L.off_partials =
         take(std::max(pair_partials, precision == LINGAM_MIXED ? gram_tc_partial_bytes(p, L.ld) : size_t(0)));
     L.off_invroot = take(P * 8);
@@ -125,7 +147,9 @@ static bool valid_opts(const lingam_opts& o) {
     return (o.precision == LINGAM_MIXED || o.precision == LINGAM_FP64) &&
            (o.input_dtype == LINGAM_F32 || o.input_dtype == LINGAM_F64) && (o.prune == 0 || o.prune == 1) &&
            (o.reuse == 0 || o.reuse == 1) && o.split_n >= 0 && (o.tile_i == 0 || o.tile_i == 32 || o.tile_i == 64) &&
-           (o.tile_j == 0 || o.tile_j == 16 || o.tile_j == 32) && !(o.tile_i == 32 && o.tile_j == 16);
+           (o.tile_j == 0 || o.tile_j == 16 || o.tile_j == 32) && !(o.tile_i == 32 && o.tile_j == 16) &&
+           std::isfinite(o.gamma0) && o.gamma0 >= 0.0 &&
+           (o.gamma0 == 0.0 || (o.prune == 1 && o.reuse == 1 && std::isfinite(o.gamma_c) && o.gamma_c > 1.0));
 }
 
 static bool is_device_ptr(const void* ptr) {
@@ -135,6 +159,32 @@ static bool is_device_ptr(const void* ptr) {
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// CUDA events of the calls made by one host thread on one device: created on first need,
+// reused by every later call (each call synchronises its stream before it returns, so no
+// event is still pending when the next call records it), destroyed when the thread ends.
+struct EventPool {
+    std::vector<cudaEvent_t> ev;
+    bool reserve(size_t k) {
+        while (ev.size() < k) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            ev.push_back(e);
+        }
+        return true;
+    }
+    ~EventPool() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        cudaGetLastError();
+    }
+};
+static EventPool* event_pool(int dev) {
+    thread_local std::map<int, EventPool> pools;
+    return &pools[dev];
 }
 
 // The device view of one problem laid out in `base` (a workspace region of layout L).
@@ -184,6 +234,10 @@ static Fit make_fit(char* base, const Layout& L, int p, int n, const lingam_opts
     f.ctl = reinterpret_cast<Ctl*>(base + L.off_ctl);
     f.maxtiles = L.maxtiles;
     f.maxsplit = L.maxsplit;
+    f.nslots = L.nslots;
+    f.split_n = o.split_n;
+    f.gamma0 = o.gamma0;
+    f.gamma_c = o.gamma_c;
     const TileShape ts = o.precision == LINGAM_MIXED ? choose_tile(p, n, o.tile_i, o.tile_j) : TileShape{32, 32};
     f.tile_rows = ts.rows;
     f.tile_cols = ts.cols;
@@ -279,15 +333,25 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
     CK(cudaMemsetAsync(f.rep_margin, 0, size_t(p) * 8, st));
     const int iters = (o.max_iters > 0 && o.max_iters < p) ? o.max_iters : p;
     const bool want_B = B != nullptr && iters == p;
-    cudaEvent_t ev[5];
-    for (int k = 0; k < 5; ++k) CK(cudaEventCreate(&ev[k]));
+    // the call's events come from this host thread's pool (created once, reused by every call)
+    EventPool* pool = event_pool(dev);
+    if (!pool || !pool->reserve(5 + (o.timing ? size_t(iters) + 1 : 0))) return LINGAM_ECUDA;
+    const cudaEvent_t* ev = pool->ev.data();
+    size_t next_ev = 5;
     std::vector<cudaEvent_t> pev;   // per-iteration pair-phase events (opts.timing)
     long long launches = 0;
     int status = LINGAM_OK;
     do {
         if (cudaEventRecord(ev[0], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
-        if (launch_standardize(f, xdev, o.input_dtype, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+        if (inject_fault("standardize") || launch_standardize(f, xdev, o.input_dtype, st) != cudaSuccess) {
+            status = LINGAM_ECUDA;
+            break;
+        }
         if (cudaEventRecord(ev[1], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+        if (inject_fault("covariance")) {
+            status = LINGAM_ECUDA;
+            break;
+        }
         if (o.precision == LINGAM_MIXED) {
             if (launch_gram_tc(f, base + L.off_xin, f.partials, st) != cudaSuccess) {
                 status = LINGAM_ECUDA;
@@ -312,34 +376,27 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
         // opts.timing: one event before the first launch and one after each, so launch it
         // is timed between events it and it + 1 (consecutive launches share an event)
         if (o.timing) {
-            cudaEvent_t e0 = nullptr;
-            if (cudaEventCreate(&e0) != cudaSuccess) {
-                status = LINGAM_ECUDA;
-                break;
-            }
+            const cudaEvent_t e0 = ev[next_ev++];
             pev.push_back(e0);
             cudaEventRecord(e0, st);
         }
         for (int it = 0; it < iters && status == LINGAM_OK; ++it) {
             cudaEvent_t e1 = nullptr;
             if (o.timing) {
-                if (cudaEventCreate(&e1) != cudaSuccess) {
-                    status = LINGAM_ECUDA;
-                    break;
-                }
+                e1 = ev[next_ev++];
                 pev.push_back(e1);
             }
             // the candidate orders alternate between the two lists: iteration it reads the
             // one the previous launch planned and plans the next into the other
             Fit fi = f;
             if (it & 1) std::swap(fi.sigma, fi.sigma_alt);
-            if (launch_iteration(fi, it, grid, st) != cudaSuccess) status = LINGAM_ECUDA;
+            if (inject_fault("iteration", it) || launch_iteration(fi, it, grid, st) != cudaSuccess) status = LINGAM_ECUDA;
             ++launches;
             if (o.timing) cudaEventRecord(e1, st);
         }
         if (status != LINGAM_OK) break;
         if (cudaEventRecord(ev[3], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
-        if (want_B && launch_fit_B(f, st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
+        if (want_B && (inject_fault("bfit") || launch_fit_B(f, st) != cudaSuccess)) { status = LINGAM_ECUDA; break; }
         if (want_B) launches += 4;
         if (cudaEventRecord(ev[4], st) != cudaSuccess) { status = LINGAM_ECUDA; break; }
     } while (0);
@@ -384,6 +441,7 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
             rep->t_compute_ms = o.timing ? double(ch.phase_ns[0]) * 1e-6 : 0.0;
             rep->t_merge_ms = o.timing ? double(ch.phase_ns[1]) * 1e-6 : 0.0;
             rep->t_remove_ms = o.timing ? double(ch.phase_ns[2]) * 1e-6 : 0.0;
+            rep->threshold_updates = ch.gsteps;
         }
         if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) status = LINGAM_ECUDA;
         if (rep && status == LINGAM_OK) {
@@ -400,8 +458,17 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
             }
         }
     }
-    for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
-    for (cudaEvent_t e : pev) cudaEventDestroy(e);
+    if (log_level() >= 1) {
+        float t[4] = {-1.f, -1.f, -1.f, -1.f};
+        if (status == LINGAM_OK)
+            for (int k = 0; k < 4; ++k)
+                if (cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]) != cudaSuccess) t[k] = -1.f;
+        std::fprintf(stderr,
+                     "lingam: %s p=%d n=%d precision=%s status=%d (%s) launches=%lld ms: standardize %.3f covariance "
+                     "%.3f order %.3f B %.3f\n",
+                     cov_out ? "covariance" : "fit", p, n, o.precision == LINGAM_MIXED ? "mixed" : "fp64", status,
+                     lingam_status_string(status), launches, t[0], t[1], t[2], t[3]);
+    }
     cudaGetLastError();
     return status;
 #undef CK
@@ -485,10 +552,43 @@ struct GraphKey {
                std::tie(o.ws, o.count, o.precision, o.input_dtype, o.prune, o.reuse, o.with_B, o.shape);
     }
 };
+// Executable graphs of batch calls, by key.  At most kMaxGraphs are kept: capturing one more
+// destroys the least recently launched graph that no call is using.  Keys seen once (run
+// eagerly, captured on their next call) are forgotten all together past kMaxGraphSeen.
+struct GraphEntry {
+    cudaGraphExec_t exec;
+    unsigned long long last;   // g_graph_clock at its last launch
+    int busy;                  // calls between taking it and synchronising their stream
+};
+constexpr size_t kMaxGraphs = 32;
+constexpr size_t kMaxGraphSeen = 1024;
 static std::mutex g_graph_mu;
-static std::map<GraphKey, cudaGraphExec_t> g_graphs;
+static std::map<GraphKey, GraphEntry> g_graphs;
+static unsigned long long g_graph_clock = 0;
+static std::map<GraphKey, int> g_graph_seen;
 
-static std::map<GraphKey, int> g_graph_seen;   // keys run once eagerly, captured on the next call
+// Room for one more graph (caller holds g_graph_mu).
+static void evict_graphs() {
+    while (g_graphs.size() >= kMaxGraphs) {
+        auto lru = g_graphs.end();
+        for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it)
+            if (it->second.busy == 0 && (lru == g_graphs.end() || it->second.last < lru->second.last)) lru = it;
+        if (lru == g_graphs.end()) return;   // every graph is in use: the new one is added anyway
+        cudaGraphExecDestroy(lru->second.exec);
+        g_graphs.erase(lru);
+    }
+}
+
+// Marks a cached graph as in use for the rest of a call's scope.
+struct GraphUse {
+    const GraphKey* key = nullptr;
+    ~GraphUse() {
+        if (!key) return;
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        auto it = g_graphs.find(*key);
+        if (it != g_graphs.end() && it->second.busy > 0) --it->second.busy;
+    }
+};
 
 // Streams for the independent per-problem launches of a batch (the covariances): forked
 // from the caller's stream by an event and joined back into it, so that they run
@@ -592,7 +692,8 @@ static int fit_many(std::vector<BatchItem>& items, void* workspace, const lingam
                     const BootSrc* boot) {
     const int count = int(items.size());
     if (count == 0) return LINGAM_OK;
-    if (!valid_opts(o) || o.forced_order || o.prior || o.max_iters != 0 || !workspace) return LINGAM_EINVAL;
+    if (!valid_opts(o) || o.forced_order || o.prior || o.max_iters != 0 || o.gamma0 != 0.0 || !workspace)
+        return LINGAM_EINVAL;
     if (!is_device_ptr(workspace) || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return LINGAM_EINVAL;
     std::vector<long long> P(static_cast<size_t>(count)), N(static_cast<size_t>(count));
     bool with_B = true, gather = true;
@@ -694,12 +795,26 @@ static int fit_many(std::vector<BatchItem>& items, void* workspace, const lingam
     const GraphKey key{workspace, count, o.precision, o.input_dtype, o.prune, o.reuse, (with_B ? 1 : 0) | (gather ? 2 : 0) | (boot ? 4 : 0), shape};
     cudaGraphExec_t exec = nullptr;
     bool capture = false;
+    GraphUse use;
     if (st != nullptr) {
         std::lock_guard<std::mutex> lk(g_graph_mu);
         auto itg = g_graphs.find(key);
-        if (itg != g_graphs.end()) exec = itg->second;
-        else if (g_graph_seen.count(key)) capture = true;
-        else g_graph_seen[key] = 1;
+        if (itg != g_graphs.end()) {
+            exec = itg->second.exec;
+            itg->second.last = ++g_graph_clock;
+            ++itg->second.busy;
+            use.key = &key;
+        } else if (g_graph_seen.count(key)) {
+            capture = true;
+        } else {
+            if (g_graph_seen.size() >= kMaxGraphSeen) g_graph_seen.clear();
+            g_graph_seen[key] = 1;
+        }
+    }
+    if (inject_fault("batch")) {
+        cudaStreamSynchronize(st);   // the copies already issued finish before the call returns
+        cudaGetLastError();
+        return LINGAM_ECUDA;
     }
     if (exec) {
         CKB(cudaGraphLaunch(exec, st));
@@ -712,8 +827,17 @@ static int fit_many(std::vector<BatchItem>& items, void* workspace, const lingam
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
         if (ok) {
-            std::lock_guard<std::mutex> lk(g_graph_mu);
-            g_graphs[key] = exec;
+            {
+                std::lock_guard<std::mutex> lk(g_graph_mu);
+                evict_graphs();
+                auto ins = g_graphs.emplace(key, GraphEntry{exec, ++g_graph_clock, 1});
+                if (!ins.second) {   // another thread captured the same key meanwhile
+                    cudaGraphExecDestroy(exec);
+                    exec = ins.first->second.exec;
+                    ++ins.first->second.busy;
+                }
+                use.key = &key;
+            }
             CKB(cudaGraphLaunch(exec, st));
         } else {
             CKB(enqueue_batch(ws, BL, fits, Ls, o, rows, with_B, gather, nsm, st));
@@ -774,6 +898,10 @@ static int fit_many(std::vector<BatchItem>& items, void* workspace, const lingam
         if (status_out) status_out[k] = stk;
         if (stk != LINGAM_OK && first == LINGAM_OK) first = stk;
     }
+    if (log_level() >= 1)
+        std::fprintf(stderr, "lingam: batch count=%d rows=%d %s status=%d (%s) graph=%s\n", count, rows,
+                     boot ? "bootstrap" : "datasets", first, lingam_status_string(first),
+                     exec ? "replayed" : (capture ? "captured" : "eager"));
     cudaGetLastError();
     return first;
 #undef CKB
@@ -793,6 +921,7 @@ void lingam_default_opts(lingam_opts* o) {
     o->prune = 1;
     o->reuse = 1;
     o->timeout_s = 10.0;
+    o->gamma_c = 2.0;
 }
 
 size_t lingam_workspace_size(long long p, long long n, const lingam_opts* opts) {
@@ -918,7 +1047,7 @@ int lingam_fit_bootstrap(const void* X, long long p, long long n, int nboot, con
 }
 
 int lingam_selftest_wait(int which, double timeout_s, int* observed) {
-    if (which < 0 || which > 2 || !(timeout_s > 0.0) || timeout_s > 60.0 || !observed) return LINGAM_EINVAL;
+    if (which < 0 || which > 3 || !(timeout_s > 0.0) || timeout_s > 60.0 || !observed) return LINGAM_EINVAL;
     int st = 0;
     if (run_wait_selftest(which, (unsigned long long)(timeout_s * 1e9), &st, nullptr) != cudaSuccess) {
         cudaGetLastError();
@@ -936,6 +1065,7 @@ const char* lingam_status_string(int s) {
         case LINGAM_ENOMEM: return "out of memory";
         case LINGAM_ECUDA: return "CUDA error";
         case LINGAM_ETIMEOUT: return "device-side wait timed out";
+        case LINGAM_EBOUNDS: return "index out of bounds (debug build)";
         default: return "unknown status";
     }
 }

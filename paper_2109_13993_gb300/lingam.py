@@ -17,6 +17,7 @@ import numpy as np
 from . import build as _build
 
 LINGAM_OK, LINGAM_EINVAL, LINGAM_EDEGENERATE, LINGAM_ENOMEM, LINGAM_ECUDA, LINGAM_ETIMEOUT = 0, -1, -2, -3, -4, -5
+LINGAM_EBOUNDS = -6
 LINGAM_FP64, LINGAM_MIXED = 0, 1
 LINGAM_F32, LINGAM_F64 = 0, 1
 
@@ -30,7 +31,7 @@ class Opts(ctypes.Structure):
                 ("reuse", ctypes.c_int), ("tile_i", ctypes.c_int), ("tile_j", ctypes.c_int),
                 ("split_n", ctypes.c_int), ("timeout_s", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("forced_order", _c_int_p), ("max_iters", ctypes.c_int), ("timing", ctypes.c_int),
-                ("prior", ctypes.c_void_p)]
+                ("prior", ctypes.c_void_p), ("gamma0", ctypes.c_double), ("gamma_c", ctypes.c_double)]
 
 
 class Report(ctypes.Structure):
@@ -39,7 +40,8 @@ class Report(ctypes.Structure):
                 ("t_order_ms", ctypes.c_double), ("t_B_ms", ctypes.c_double), ("pairs_total", ctypes.c_longlong),
                 ("pairs_unpruned", ctypes.c_longlong), ("t_pair_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_longlong), ("t_pair_iter_ms", _c_dbl_p),
-                ("t_compute_ms", ctypes.c_double), ("t_merge_ms", ctypes.c_double), ("t_remove_ms", ctypes.c_double)]
+                ("t_compute_ms", ctypes.c_double), ("t_merge_ms", ctypes.c_double), ("t_remove_ms", ctypes.c_double),
+                ("threshold_updates", ctypes.c_longlong)]
 
 
 class LingamError(RuntimeError):
@@ -56,11 +58,12 @@ def lib_path() -> str:
 
 
 def load():
-    """Load the CUDA library (raises if it has not been built)."""
+    """Load the CUDA library (raises if it has not been built).  The environment variable
+    LINGAM_LIBRARY may name another build of it (e.g. build.DEBUG_LIB)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = os.environ.get("LINGAM_LIBRARY") or _build.LIB
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library {path} is missing: build it with "
                            "`python -c 'import __graft_entry__ as g; g.build()'`")
@@ -120,7 +123,8 @@ def status_string(status: int) -> str:
 
 def make_opts(precision: str = "mixed", input_dtype=np.float32, prune: bool = True, reuse: bool = True,
               split_n: int = 0, timeout_s: float = 10.0, stream=None, forced_order=None, max_iters: int = 0,
-              timing: bool = False, tile_i: int = 0, tile_j: int = 0, prior=None) -> tuple[Opts, object]:
+              timing: bool = False, tile_i: int = 0, tile_j: int = 0, prior=None, gamma0: float = 0.0,
+              gamma_c: float = 2.0) -> tuple[Opts, object]:
     o = Opts()
     load().lingam_default_opts(ctypes.byref(o))
     o.precision = {"mixed": LINGAM_MIXED, "fp64": LINGAM_FP64}[precision]
@@ -134,6 +138,8 @@ def make_opts(precision: str = "mixed", input_dtype=np.float32, prune: bool = Tr
     o.timing = int(bool(timing))
     o.tile_i = int(tile_i)
     o.tile_j = int(tile_j)
+    o.gamma0 = float(gamma0)
+    o.gamma_c = float(gamma_c)
     keep = []
     if forced_order is not None:
         fo = np.ascontiguousarray(forced_order, dtype=np.int32)
@@ -164,6 +170,7 @@ class FitResult:
     pairs_unpruned: int = 0
     kernel_launches: int = 0
     t_pair_iter_ms: np.ndarray | None = None
+    threshold_updates: int = 0
 
 
 def _torch():
@@ -202,16 +209,17 @@ def _data_ptr(X):
 def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, forced_order=None,
         want_scores: bool = False, want_B: bool = True, split_n: int = 0, timeout_s: float = 10.0,
         stream=None, workspace=None, max_iters: int = 0, timing: bool = False, out=None,
-        tile_i: int = 0, tile_j: int = 0, prior=None) -> FitResult:
+        tile_i: int = 0, tile_j: int = 0, prior=None, gamma0: float = 0.0, gamma_c: float = 2.0) -> FitResult:
     """lingam_fit on X (p x n, numpy on the host or a torch tensor on the GPU).  prior: None
-    or a p x p int8 array, prior[i, j] = 1 when X_j is a known ancestor of X_i."""
+    or a p x p int8 array, prior[i, j] = 1 when X_j is a known ancestor of X_i.  gamma0 > 0:
+    the paper's threshold schedule (start gamma0, growth gamma_c) instead of the running bound."""
     L = load()
     ptr, p, n, dt, keep = _data_ptr(X)
     torch = _torch()
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     o, keep_forced = make_opts(precision, dt, prune, reuse, split_n, timeout_s, stream, forced_order, max_iters,
-                               timing, tile_i, tile_j, prior)
+                               timing, tile_i, tile_j, prior, gamma0, gamma_c)
     need = int(L.lingam_workspace_size(p, n, ctypes.byref(o)))
     if need == 0:
         raise LingamError(LINGAM_EINVAL, "invalid sizes or options")
@@ -245,7 +253,8 @@ def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, for
                                "order": rep.t_order_ms, "B": rep.t_B_ms, "pair": rep.t_pair_ms,
                                "compute": rep.t_compute_ms, "merge": rep.t_merge_ms, "remove": rep.t_remove_ms},
                      pairs_total=int(rep.pairs_total), pairs_unpruned=int(rep.pairs_unpruned),
-                     kernel_launches=int(rep.kernel_launches), t_pair_iter_ms=tpi)
+                     kernel_launches=int(rep.kernel_launches), t_pair_iter_ms=tpi,
+                     threshold_updates=int(rep.threshold_updates))
 
 
 def covariance(X, precision: str = "mixed", stream=None, workspace=None, out=None):

@@ -116,7 +116,7 @@ def test_batch_rejects_bad_arguments_without_gpu_work(lib):
 
 def test_selftest_wait_rejects_bad_arguments_without_gpu_work(lib):
     obs = ctypes.c_int(-7)
-    assert lib.lingam_selftest_wait(3, 0.05, ctypes.byref(obs)) == lingam.LINGAM_EINVAL
+    assert lib.lingam_selftest_wait(4, 0.05, ctypes.byref(obs)) == lingam.LINGAM_EINVAL
     assert lib.lingam_selftest_wait(-1, 0.05, ctypes.byref(obs)) == lingam.LINGAM_EINVAL
     assert lib.lingam_selftest_wait(0, 0.0, ctypes.byref(obs)) == lingam.LINGAM_EINVAL
     assert lib.lingam_selftest_wait(0, 120.0, ctypes.byref(obs)) == lingam.LINGAM_EINVAL
@@ -158,3 +158,29 @@ def test_prior_knowledge_is_validated_without_gpu_work(lib):
     # the workspace of a fit with prior knowledge holds the p x p matrix and the counts
     o, keep = lingam.make_opts(prior=-np.ones((p, p), dtype=np.int8))
     assert lib.lingam_workspace_size(100, 1000, ctypes.byref(o)) >= lingam.workspace_size(100, 1000) + 100 * 100
+
+
+def test_threshold_schedule_options_are_validated(lib):
+    """opts.gamma0 > 0 (the paper's threshold schedule) needs gamma_c > 1 and pruning with
+    reuse; negative or non-finite values, and batches, are rejected without device work."""
+    def size(**kw):
+        o, _ = lingam.make_opts(**kw)
+        return lib.lingam_workspace_size(50, 1000, ctypes.byref(o))
+    assert size(gamma0=1e-3, gamma_c=2.0) == size() > 0
+    for kw in ({"gamma0": -1.0}, {"gamma0": float("nan")}, {"gamma0": float("inf")},
+               {"gamma0": 1e-3, "gamma_c": 1.0}, {"gamma0": 1e-3, "gamma_c": float("inf")},
+               {"gamma0": 1e-3, "prune": False}, {"gamma0": 1e-3, "reuse": False}):
+        assert size(**kw) == 0, kw
+    o = lingam.Opts()
+    lib.lingam_default_opts(ctypes.byref(o))
+    assert o.gamma0 == 0.0 and o.gamma_c == 2.0
+    x = np.zeros((3, 10), dtype=np.float32)
+    xp = (ctypes.c_void_p * 1)(x.ctypes.data)
+    ps = (ctypes.c_longlong * 1)(3)
+    ns = (ctypes.c_longlong * 1)(10)
+    order = np.zeros(3, dtype=np.int32)
+    op = (ctypes.c_void_p * 1)(order.ctypes.data)
+    ws = np.zeros(1 << 20, dtype=np.uint8)
+    og, _ = lingam.make_opts(gamma0=1e-3)
+    assert lib.lingam_fit_batch(1, xp, ps, ns, op, None, ctypes.c_void_p(ws.ctypes.data), ctypes.byref(og),
+                                None, None) == lingam.LINGAM_EINVAL

@@ -190,6 +190,28 @@ def test_pruning_and_reuse_do_not_change_the_result(precision):
         assert np.allclose(noreuse.root_score, full.root_score, rtol=1e-5, atol=1e-9)
 
 
+# ---------------------------------------------------------------- sample-axis split (opts.split_n)
+
+@pytest.mark.parametrize("name,split_n", [("p100_n10000", 1), ("p100_n10000", 2), ("p100_n10000", 7),
+                                          ("p20_n2000", 1)])
+def test_split_n_matches_oracle_and_default(name, split_n):
+    """Capping the CTAs per tile (split_n = s) changes only how a pair's samples are cut into
+    CTA segments: every score stays within the mixed-path tolerance of the oracle along the
+    oracle's order, within FP32 rounding of the default split, and the free-run order is the
+    default's."""
+    d = synth.workload(name, seed=1)
+    X32 = d.X.astype(np.float32)
+    o_order, o_B, o_S = oracle.fit(X32.astype(np.float64))
+    X = _dev(X32, torch.float32)
+    res = lingam.fit(X, prune=False, forced_order=o_order, want_scores=True, split_n=split_n)
+    ref = lingam.fit(X, prune=False, forced_order=o_order, want_scores=True)
+    tau = _check_scores(res.scores, o_S, rtol=0.0, atol=1e-4)
+    _check_scores(res.scores, ref.scores, rtol=1e-5, atol=1e-8)
+    free = lingam.fit(X, split_n=split_n)
+    assert np.array_equal(free.order, lingam.fit(X).order)
+    print(f"{name} split_n={split_n}: max score error {tau.max():.2e}")
+
+
 # ---------------------------------------------------------------- worked example of the paper
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
@@ -317,6 +339,53 @@ def test_p300_mixed_pruned_every_iteration_vs_oracle(p300):
     print(f"p=300 n=5000 q=6/299 mixed, pruned: max score error {max(taus):.2e}; {resolved} of 299 iterations "
           f"resolved and equal to the oracle's argmin; {np.mean(completes):.1f} complete variables per iteration "
           f"on average; B error {eB:.1e}; free run equal to the oracle on the first {upto} iterations")
+
+
+@pytest.mark.parametrize("start,gamma_c", [("low", 2.0), ("high", 10.0)])
+def test_p300_paper_threshold_schedule_every_iteration_vs_oracle(p300, start, gamma_c):
+    """The paper's own threshold schedule (opts.gamma0 > 0: start gamma0, raised by gamma_c
+    until some variable can finish below it; Sec. III-B/C, Algorithms 6 and 9) in place of
+    the running bound, forced along the oracle's order: every iteration passes the same
+    checks as the default schedule (complete scores within 1e-4 of the oracle, resolved
+    argmins equal, stopped variables never below the root), and the free run gives the
+    default run's order.  A start below every root score must be raised; one above every
+    root score never is, and then evaluates at least as many pairs as the running bound."""
+    X32, X64, o_order, o_B, o_S = p300
+    X = _dev(X32, torch.float32)
+    ref = lingam.fit(X)
+    rs = ref.root_score[ref.root_score > 0]
+    gamma0 = 1e-3 * rs.min() if start == "low" else 10.0 * rs.max()
+    res = lingam.fit(X, forced_order=o_order, want_scores=True, gamma0=gamma0, gamma_c=gamma_c)
+    margins = _margins(o_S)
+    for it in range(300):
+        tau, groot, nc, gap = _check_pruned_iteration(res.scores[it], o_S[it], 1e-4)
+        if margins[it] > 2 * tau and it < 299:
+            assert groot == o_order[it], f"iteration {it}"
+    free = lingam.fit(X, gamma0=gamma0, gamma_c=gamma_c)
+    assert np.array_equal(free.order, ref.order)
+    assert np.allclose(free.root_score, ref.root_score, rtol=1e-4, atol=1e-9)
+    assert ref.threshold_updates == 0
+    if start == "low":
+        assert free.threshold_updates >= len(rs)   # every iteration whose root scores above 0
+    else:
+        assert free.threshold_updates == 0 and free.pairs_total >= ref.pairs_total
+    print(f"p=300 gamma0={gamma0:.3g} c={gamma_c}: pairs {free.pairs_total} (running bound {ref.pairs_total}, "
+          f"unpruned {ref.pairs_unpruned}), threshold raised {free.threshold_updates} times")
+
+
+def test_threshold_schedule_limits():
+    """gamma0 above every score prunes nothing (every pair evaluated, no raise); on the FP64
+    path the schedule's roots and root scores equal the running bound's to FP64 rounding."""
+    d = synth.workload("p100_n10000", seed=2)
+    X32 = _dev(d.X.astype(np.float32), torch.float32)
+    big = lingam.fit(X32, gamma0=1e30)
+    assert big.pairs_total == big.pairs_unpruned and big.threshold_updates == 0
+    X64 = _dev(d.X, torch.float64)
+    a = lingam.fit(X64, precision="fp64")
+    b = lingam.fit(X64, precision="fp64", gamma0=1e-3 * a.root_score[a.root_score > 0].min(), gamma_c=3.0)
+    assert np.array_equal(a.order, b.order)
+    assert np.allclose(a.root_score, b.root_score, rtol=1e-12, atol=1e-15)
+    assert b.threshold_updates >= int((a.root_score > 0).sum())
 
 
 def test_p300_fp64_path_every_iteration_vs_oracle(p300):
