@@ -192,8 +192,10 @@ def batched_workload(lingam, synth, torch, dev, stream, reps: int = 5) -> dict:
     """The batched configuration: 256 bootstrap resamples of one p=50, n=2000 dataset
     and 64 datasets with p in 20..120, n in 500..8000 (FP32, mixed path), each set one
     library call; inputs resident on the device; after two calls (eager, graph capture)
-    the replayed graph is timed with CUDA events.  Next to it, every member of each set as
-    a sequential single fit through lingam_fit (one workspace reused), timed as a whole."""
+    the replayed graph is timed with CUDA events, with every tile shape of the batch kernel
+    and with the shape the batch autotuner picks for each set.  Next to it, every member of
+    each set as a sequential single fit through lingam_fit (one workspace reused), timed as
+    a whole."""
     import ctypes
     d = synth.lingam_dataset(50, 2000, 4.0 / 49.0, seed=5)
     X = torch.tensor(d.X.astype(np.float32), device=dev)
@@ -220,6 +222,16 @@ def batched_workload(lingam, synth, torch, dev, stream, reps: int = 5) -> dict:
             out.append(e0.elapsed_time(e1))
         return float(np.median(out))
 
+    # every tile shape of the batch kernel on both sets, then the batch autotuner's choice
+    # for each set's size bucket (the gathered resamples stand in for the bootstrap call)
+    Xb = [X[:, idx[b].long()].contiguous() for b in range(idx.shape[0])]
+    shapes_ms = {"bootstrap_256": {}, "uneven_64": {}}
+    for ti, tj in ((64, 32), (32, 32), (64, 16)):
+        shapes_ms["bootstrap_256"][f"{ti}x{tj}"] = timed(
+            lambda: lingam.fit_bootstrap(X, idx, workspace=wsb, tile_i=ti, tile_j=tj))
+        shapes_ms["uneven_64"][f"{ti}x{tj}"] = timed(lambda: lingam.fit_batch(Xs, workspace=wsu, tile_i=ti, tile_j=tj))
+    lingam.autotune_reset()
+    tuned = {"bootstrap_256": lingam.autotune_batch(Xb)[0], "uneven_64": lingam.autotune_batch(Xs, workspace=wsu)[0]}
     t_boot = timed(lambda: lingam.fit_bootstrap(X, idx, workspace=wsb))
     t_unev = timed(lambda: lingam.fit_batch(Xs, workspace=wsu))
     # useful work: the pairs each problem's fit evaluated (reports of one more call) x its n
@@ -228,7 +240,6 @@ def batched_workload(lingam, synth, torch, dev, stream, reps: int = 5) -> dict:
     ps_boot = sum(float(np.sum(pp)) * 2000 for pp in rb.pairs)
     ps_unev = sum(float(np.sum(pp)) * x.shape[1] for pp, x in zip(ru.pairs, Xs))
     # every member as a sequential single fit (one workspace of the largest size, reused)
-    Xb = [X[:, idx[b].long()].contiguous() for b in range(idx.shape[0])]
     ws1 = lingam.alloc_workspace(lingam.workspace_size(50, 2000), device=dev)
     for x in Xb[:2]:
         lingam.fit(x, workspace=ws1)
@@ -256,7 +267,10 @@ def batched_workload(lingam, synth, torch, dev, stream, reps: int = 5) -> dict:
             "speedup_vs_sequential": {"bootstrap_256": seq_boot / t_boot, "uneven_64": seq_unev / t_unev},
             "pair_samples_evaluated": {"bootstrap_256": ps_boot, "uneven_64": ps_unev},
             "pair_samples_per_s": {"bootstrap_256": ps_boot / (t_boot / 1e3), "uneven_64": ps_unev / (t_unev / 1e3)},
-            "timing": "median of 5 graph replays, CUDA events; inputs on the device"}
+            "tile_shape": {k: f"{v[0]}x{v[1]}" for k, v in tuned.items()},
+            "tile_shapes_ms": shapes_ms,
+            "timing": "median of 5 graph replays, CUDA events; inputs on the device; tile shape chosen by "
+                      "lingam_autotune_batch for each set's size bucket"}
 
 
 def cpu_model() -> str:
@@ -327,9 +341,14 @@ def configs_table(lingam, synth, torch, dev, stream, seeds=(1, 2, 3, 4, 5), reps
                     s64 = lingam.fit(X64, precision="fp64", workspace=ws64, prune=False, want_scores=True,
                                      max_iters=it + 1).scores[it]
                     a, b = s64[int(o64[it])], s64[int(om[it])]
+                    # the mixed path's per-score error bound at this iteration (kappa = 1.6e-6 as
+                    # measured against the oracle, m = partners per variable)
+                    m = p - it - 1
+                    tau = 1.6e-6 * np.sqrt(m * max(float(b), 0.0)) + m * 4e-12
                     row["first_divergence"] = {"iteration": it, "fp64_score_fp64_root": float(a),
                                                "fp64_score_mixed_root": float(b),
-                                               "relative_gap": float((b - a) / abs(a)) if a else None}
+                                               "relative_gap": float((b - a) / abs(a)) if a else None,
+                                               "gap_over_mixed_score_bound": float((b - a) / tau)}
             rows.append(row)
             del ws64
         table[name] = rows
@@ -544,6 +563,10 @@ def run_ours(args, rank: int, world: int):
     comp = float(np.mean(pairs)) * n / (float(np.mean([x[0] for x in phases])) / 1000.0)
     roofline["compute_phase"] = {"achieved": comp / 1e9, "frac": comp / peak,
                                  "ms_per_step": {"pair_compute": ph[0], "merge_finalize": ph[1], "removal": ph[2]}}
+    # the pair tiles' own efficiency: useful pairs over the pairs the waves' tiles computed
+    roofline["waves_per_step"] = int(rt.waves)
+    roofline["tile_pairs_per_step"] = int(rt.tile_pairs)
+    roofline["useful_fraction_of_tile_pairs"] = float(rt.pairs_total) / max(1, int(rt.tile_pairs))
 
     line = {"metric": METRIC if (p, n) == (P_DEFAULT, N_DEFAULT) else
             f"pair-sample evals/s (unpruned-equivalent) at p={p}, n={n}",

@@ -144,6 +144,10 @@ typedef struct {
     long long threshold_updates; /* opts.gamma0 > 0: times the threshold was multiplied by gamma_c,
                                     summed over the iterations (each one a kernel launch and a
                                     read-back in the paper's host loop, Algorithm 9); else 0 */
+    long long waves;             /* pair waves run over the fit (single fits) */
+    long long tile_pairs;        /* pairs the waves' tiles computed: tiles x rows x columns, row
+                                    padding, unused columns and the duplicate half of the
+                                    columns' own block included (pairs_total are the useful ones) */
 } lingam_report;
 
 /* Fills *opts with the defaults: MIXED, F32, prune = reuse = 1, autotuned
@@ -206,13 +210,31 @@ int lingam_covariance(const void* X, long long p, long long n, double* Sigma, vo
  *                       ms is not NULL) receive the ordering times with 64 x 32, 32 x 32
  *                       and 64 x 16 tiles.  Costs three fits; the workspace is as for
  *                       lingam_fit.
- * lingam_autotune_reset -- forgets every measured choice.
- * The table is shared by all threads of the process (guarded by a mutex).
+ * lingam_batch_tile_rows, lingam_batch_tile_cols -- the shape lingam_fit_batch and
+ *                       lingam_fit_bootstrap use on the mixed path for a batch whose
+ *                       largest problem has maxp variables and maxn samples, when
+ *                       opts->tile_i and opts->tile_j are 0.  Batches have a table of their
+ *                       own (bucket of the largest p and n); a bucket never measured uses
+ *                       32 x 32, which pads least once problems are down to r < 32.
+ * lingam_autotune_batch -- measures lingam_fit_batch on the caller's count datasets (as
+ *                       lingam_fit_batch with opts on the mixed path, B not fitted) with
+ *                       each shape: a warm-up call, the call that captures the graph, and
+ *                       the timed third call (host wall time of the synchronous call).
+ *                       Records the fastest for the bucket of the batch's largest p and n,
+ *                       returns it in *tile_rows, *tile_cols, and ms[0..2] as for
+ *                       lingam_autotune.  Costs nine batch calls; the workspace is as for
+ *                       lingam_fit_batch.  LINGAM_EINVAL for the FP64 path.
+ * lingam_autotune_reset -- forgets every measured choice (both tables).
+ * The tables are shared by all threads of the process (guarded by a mutex).
  */
 int lingam_tile_rows(long long p, long long n);
 int lingam_tile_cols(long long p, long long n);
 int lingam_autotune(const void* X, long long p, long long n, void* workspace, const lingam_opts* opts,
                     int* tile_rows, int* tile_cols, double* ms);
+int lingam_batch_tile_rows(long long maxp, long long maxn);
+int lingam_batch_tile_cols(long long maxp, long long maxn);
+int lingam_autotune_batch(int count, const void* const* X, const long long* p, const long long* n, void* workspace,
+                          const lingam_opts* opts, int* tile_rows, int* tile_cols, double* ms);
 void lingam_autotune_reset(void);
 
 /*
@@ -249,8 +271,10 @@ size_t lingam_workspace_size_batch(int count, const long long* p, const long lon
  * graph on the second call with the same workspace and problem shapes (and options),
  * and replayed by every later such call; calls on the legacy default stream (NULL)
  * run without a graph.  opts->forced_order and opts->prior must be NULL, and
- * opts->max_iters and opts->gamma0 0; opts->split_n is ignored; the pair tiles are
- * 32 x 32 on both paths.
+ * opts->max_iters and opts->gamma0 0; opts->split_n is ignored.  Pair tiles: on the
+ * mixed path opts->tile_i x opts->tile_j for every problem of the call (64 x 32, 32 x 32
+ * or 64 x 16), or, with both 0, the batch autotuner's shape for the largest p and n
+ * (lingam_batch_tile_rows/_cols); 32 x 32 on the FP64 path.
  */
 int lingam_fit_batch(int count, const void* const* X, const long long* p, const long long* n, int* const* order,
                      double* const* B, void* workspace, const lingam_opts* opts, int* status,

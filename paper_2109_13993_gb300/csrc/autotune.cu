@@ -1,7 +1,8 @@
 // autotune.cu -- the pair-tile autotuner: the tile shape (rows x columns: 64 x 32,
 // 32 x 32 or 64 x 16) of the mixed path per problem-size bucket (ceil(log2 p),
-// ceil(log2 n)), measured by lingam_autotune on the caller's data and kept in a
-// process-wide table; buckets never measured use a default rule.
+// ceil(log2 n)), measured by lingam_autotune (single fits) or lingam_autotune_batch
+// (batch calls, bucket of the largest p and n) on the caller's data and kept in two
+// process-wide tables; buckets never measured use a default rule.
 #include <chrono>
 #include <cstring>
 #include <map>
@@ -44,9 +45,25 @@ void autotune_record(long long p, long long n, TileShape shape) {
     g_tune[bucket(p, n)] = shape;
 }
 
+// Batch calls: a table of its own, keyed by the batch's largest p and n.  Default: 32 x 32
+// tiles, which a batch of many small problems pads least once r < 32.
+static std::map<std::pair<int, int>, TileShape> g_tune_batch;
+
+TileShape autotune_batch_shape(long long maxp, long long maxn) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_batch.find(bucket(maxp, maxn));
+    return it != g_tune_batch.end() ? it->second : TileShape{32, 32};
+}
+
+void autotune_batch_record(long long maxp, long long maxn, TileShape shape) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_batch[bucket(maxp, maxn)] = shape;
+}
+
 void autotune_clear() {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune.clear();
+    g_tune_batch.clear();
 }
 
 }  // namespace lingam

@@ -85,6 +85,9 @@ struct Ctl {
     // at each iteration's plan, and the number of times it was raised over the fit
     double gamma;
     long long gsteps;
+    // waves run over the fit, and the pairs their tiles computed (tiles x rows x columns,
+    // padding and the mirrored half of the column block included)
+    long long waves, tile_pairs;
 };
 
 __host__ __device__ inline unsigned long long pack_wave(unsigned seq, int done, int ntiles, int ncol, int nrow) {

@@ -798,6 +798,8 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
             ctl->wave += 1;
         }
         ctl->merged = 0;
+        ctl->waves += 1;
+        ctl->tile_pairs += (long long)ntiles * TI * TJ;
         if (seq != 0) {
             // publish: the CTAs of a single fit wait for this word instead of a grid barrier
             __threadfence();
@@ -2231,11 +2233,14 @@ static cudaError_t launch_batch_cfg(const Fit* fits_dev, int count, int maxp, Ct
     return cudaLaunchKernelEx(&cfg, k_batch<Cfg>, fits_dev, count, maxp, bctl);
 }
 
-cudaError_t launch_batch(const Fit* fits_dev, int count, int maxp, int precision, Ctl* bctl, int nsm,
-                         cudaStream_t st) {
+cudaError_t launch_batch(const Fit* fits_dev, int count, int maxp, int precision, int tile_rows, int tile_cols,
+                         Ctl* bctl, int nsm, cudaStream_t st) {
     if (count < 1 || count > kBatchMax) return cudaErrorInvalidValue;
-    return precision == LINGAM_MIXED ? launch_batch_cfg<CfgF32>(fits_dev, count, maxp, bctl, nsm, st)
-                                     : launch_batch_cfg<CfgD>(fits_dev, count, maxp, bctl, nsm, st);
+    if (precision != LINGAM_MIXED) return launch_batch_cfg<CfgD>(fits_dev, count, maxp, bctl, nsm, st);
+    if (tile_rows == 64 && tile_cols == 32) return launch_batch_cfg<CfgF64>(fits_dev, count, maxp, bctl, nsm, st);
+    if (tile_rows == 64 && tile_cols == 16) return launch_batch_cfg<CfgF16>(fits_dev, count, maxp, bctl, nsm, st);
+    if (tile_rows == 32 && tile_cols == 32) return launch_batch_cfg<CfgF32>(fits_dev, count, maxp, bctl, nsm, st);
+    return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------------ bounded-wait self-test

@@ -35,9 +35,11 @@ cudaError_t launch_iteration(const Fit& f, int it, int grid, cudaStream_t st);
 int iteration_grid(const Fit& f, int nsm);
 // The ordering of up to 512 problems (a Fit table in device memory, each with its own
 // control block) in one persistent cooperative launch, all iterations, in lockstep;
-// bctl carries the launch's barrier, abort flag and timeout.
-cudaError_t launch_batch(const Fit* fits_dev, int count, int maxp, int precision, Ctl* bctl, int nsm,
-                         cudaStream_t st);
+// bctl carries the launch's barrier, abort flag and timeout.  The mixed path's pair tiles
+// are tile_rows x tile_cols (64 x 32, 32 x 32 or 64 x 16; every Fit of the table carries
+// the same shape); the FP64 path's are 32 x 32.
+cudaError_t launch_batch(const Fit* fits_dev, int count, int maxp, int precision, int tile_rows, int tile_cols,
+                         Ctl* bctl, int nsm, cudaStream_t st);
 constexpr int kBatchLaunchMax = 512;   // problems per launch_batch
 // B from the order: Cholesky of the covariance in causal order, B = I - diag(R) R^{-1}.
 cudaError_t launch_fit_B(const Fit& f, cudaStream_t st);
@@ -56,5 +58,8 @@ struct TileShape {
 TileShape autotune_tile_shape(long long p, long long n);
 void autotune_record(long long p, long long n, TileShape shape);
 void autotune_clear();
+// The same for batch calls, keyed by the batch's largest p and largest n.
+TileShape autotune_batch_shape(long long maxp, long long maxn);
+void autotune_batch_record(long long maxp, long long maxn, TileShape shape);
 
 }  // namespace lingam

@@ -3,6 +3,7 @@
 // the results.  The library allocates no memory: every buffer is carved out
 // of the caller's workspace.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -150,6 +151,14 @@ static bool valid_opts(const lingam_opts& o) {
            (o.tile_j == 0 || o.tile_j == 16 || o.tile_j == 32) && !(o.tile_i == 32 && o.tile_j == 16) &&
            std::isfinite(o.gamma0) && o.gamma0 >= 0.0 &&
            (o.gamma0 == 0.0 || (o.prune == 1 && o.reuse == 1 && std::isfinite(o.gamma_c) && o.gamma_c > 1.0));
+}
+
+// Pair-tile shape of a batch call: opts' explicit shape (mixed path), else the batch
+// autotuner's table for the largest p and n; the FP64 path has 32 x 32 tiles only.
+static TileShape batch_tile_shape(const lingam_opts& o, long long maxp, long long maxn) {
+    if (o.precision != LINGAM_MIXED) return TileShape{32, 32};
+    if (o.tile_i != 0 || o.tile_j != 0) return TileShape{o.tile_i ? o.tile_i : 64, o.tile_j ? o.tile_j : 32};
+    return autotune_batch_shape(maxp, maxn);
 }
 
 static bool is_device_ptr(const void* ptr) {
@@ -442,6 +451,8 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
             rep->t_merge_ms = o.timing ? double(ch.phase_ns[1]) * 1e-6 : 0.0;
             rep->t_remove_ms = o.timing ? double(ch.phase_ns[2]) * 1e-6 : 0.0;
             rep->threshold_updates = ch.gsteps;
+            rep->waves = ch.waves;
+            rep->tile_pairs = ch.tile_pairs;
         }
         if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) status = LINGAM_ECUDA;
         if (rep && status == LINGAM_OK) {
@@ -663,7 +674,7 @@ static cudaError_t enqueue_batch(char* ws, const BatchLayout& BL, const std::vec
         const int cnt = std::min(kBatchLaunchMax, count - c0);
         int maxp = 0;
         for (int k = c0; k < c0 + cnt; ++k) maxp = std::max(maxp, fits[size_t(k)].p);
-        e = launch_batch(fits_dev + c0, cnt, maxp, o.precision, bctl, nsm, st);
+        e = launch_batch(fits_dev + c0, cnt, maxp, o.precision, fits[0].tile_rows, fits[0].tile_cols, bctl, nsm, st);
         if (e != cudaSuccess) return e;
     }
     if (with_B) {
@@ -751,6 +762,11 @@ static int fit_many(std::vector<BatchItem>& items, void* workspace, const lingam
         shape ^= (unsigned long long)v;
         shape *= 1099511628211ull;
     };
+    // the pair-tile shape of the whole batch: the caller's, else the batch autotuner's for the
+    // largest p and n (the FP64 path: 32 x 32)
+    const TileShape ts = batch_tile_shape(o, *std::max_element(P.begin(), P.end()), *std::max_element(N.begin(), N.end()));
+    mix(ts.rows);
+    mix(ts.cols);
     for (int k = 0; k < count; ++k) {
         BatchItem& it = items[size_t(k)];
         char* base = ws + BL.region[size_t(k)];
@@ -758,8 +774,8 @@ static int fit_many(std::vector<BatchItem>& items, void* workspace, const lingam
         const Layout& L = Ls[size_t(k)];
         Fit f = make_fit(base, L, int(it.p), int(it.n), o, it.rep && it.rep->scores);
         f.ctl = reinterpret_cast<Ctl*>(ws + BL.off_ctls) + k;
-        f.tile_rows = 32;   // the batch kernel's tile shape (32 x 32 on both paths)
-        f.tile_cols = 32;
+        f.tile_rows = ts.rows;
+        f.tile_cols = ts.cols;
         fits[size_t(k)] = f;
         SrcDesc sd;
         if (boot) {
@@ -990,6 +1006,59 @@ int lingam_autotune(const void* X, long long p, long long n, void* workspace, co
 }
 
 void lingam_autotune_reset(void) { autotune_clear(); }
+
+int lingam_batch_tile_rows(long long maxp, long long maxn) {
+    if (maxp < 1 || maxn < 3) return 0;
+    return autotune_batch_shape(maxp, maxn).rows;
+}
+
+int lingam_batch_tile_cols(long long maxp, long long maxn) {
+    if (maxp < 1 || maxn < 3) return 0;
+    return autotune_batch_shape(maxp, maxn).cols;
+}
+
+int lingam_autotune_batch(int count, const void* const* X, const long long* p, const long long* n, void* workspace,
+                          const lingam_opts* opts, int* tile_rows, int* tile_cols, double* ms) {
+    lingam_opts o;
+    lingam_default_opts(&o);
+    if (opts) o = *opts;
+    if (count < 1 || !X || !p || !n || !workspace || !tile_rows || !tile_cols || o.precision != LINGAM_MIXED)
+        return LINGAM_EINVAL;
+    long long maxp = 0, maxn = 0;
+    std::vector<std::vector<int>> ord(static_cast<size_t>(count));
+    std::vector<int*> op(static_cast<size_t>(count));
+    for (int k = 0; k < count; ++k) {
+        if (p[k] < 1 || n[k] < 3 || p[k] > kMaxP) return LINGAM_EINVAL;
+        maxp = std::max(maxp, p[k]);
+        maxn = std::max(maxn, n[k]);
+        ord[size_t(k)].resize(size_t(p[k]));
+        op[size_t(k)] = ord[size_t(k)].data();
+    }
+    const TileShape cand[3] = {{64, 32}, {32, 32}, {64, 16}};
+    double t[3] = {0.0, 0.0, 0.0};
+    int best = 0;
+    for (int c = 0; c < 3; ++c) {
+        lingam_opts oc = o;
+        oc.tile_i = cand[c].rows;
+        oc.tile_j = cand[c].cols;
+        // a warm-up call, the call that captures the graph, then the timed replay (three
+        // eager calls on the legacy default stream); every call is synchronous
+        for (int rep = 0; rep < 3; ++rep) {
+            const auto t0 = std::chrono::steady_clock::now();
+            const int st = lingam_fit_batch(count, X, p, n, op.data(), nullptr, workspace, &oc, nullptr, nullptr);
+            const auto t1 = std::chrono::steady_clock::now();
+            if (st != LINGAM_OK) return st;
+            t[c] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        }
+        if (t[c] < t[best]) best = c;
+    }
+    autotune_batch_record(maxp, maxn, cand[best]);
+    *tile_rows = cand[best].rows;
+    *tile_cols = cand[best].cols;
+    if (ms)
+        for (int c = 0; c < 3; ++c) ms[c] = t[c];
+    return LINGAM_OK;
+}
 
 size_t lingam_workspace_size_batch(int count, const long long* p, const long long* n, const lingam_opts* opts) {
     lingam_opts o;

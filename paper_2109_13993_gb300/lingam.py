@@ -41,7 +41,8 @@ class Report(ctypes.Structure):
                 ("pairs_unpruned", ctypes.c_longlong), ("t_pair_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_longlong), ("t_pair_iter_ms", _c_dbl_p),
                 ("t_compute_ms", ctypes.c_double), ("t_merge_ms", ctypes.c_double), ("t_remove_ms", ctypes.c_double),
-                ("threshold_updates", ctypes.c_longlong)]
+                ("threshold_updates", ctypes.c_longlong), ("waves", ctypes.c_longlong),
+                ("tile_pairs", ctypes.c_longlong)]
 
 
 class LingamError(RuntimeError):
@@ -101,6 +102,14 @@ def load():
     L.lingam_autotune.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p,
                                   ctypes.POINTER(Opts), _c_int_p, _c_int_p, _c_dbl_p]
     L.lingam_autotune.restype = ctypes.c_int
+    L.lingam_batch_tile_rows.argtypes = [ctypes.c_longlong, ctypes.c_longlong]
+    L.lingam_batch_tile_rows.restype = ctypes.c_int
+    L.lingam_batch_tile_cols.argtypes = [ctypes.c_longlong, ctypes.c_longlong]
+    L.lingam_batch_tile_cols.restype = ctypes.c_int
+    L.lingam_autotune_batch.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), _c_ll_p, _c_ll_p,
+                                        ctypes.c_void_p, ctypes.POINTER(Opts), _c_int_p, _c_int_p,
+                                        ctypes.POINTER(ctypes.c_double)]
+    L.lingam_autotune_batch.restype = ctypes.c_int
     L.lingam_autotune_reset.argtypes = []
     L.lingam_autotune_reset.restype = None
     L.lingam_status_string.argtypes = [ctypes.c_int]
@@ -171,6 +180,8 @@ class FitResult:
     kernel_launches: int = 0
     t_pair_iter_ms: np.ndarray | None = None
     threshold_updates: int = 0
+    waves: int = 0
+    tile_pairs: int = 0
 
 
 def _torch():
@@ -254,7 +265,8 @@ def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, for
                                "compute": rep.t_compute_ms, "merge": rep.t_merge_ms, "remove": rep.t_remove_ms},
                      pairs_total=int(rep.pairs_total), pairs_unpruned=int(rep.pairs_unpruned),
                      kernel_launches=int(rep.kernel_launches), t_pair_iter_ms=tpi,
-                     threshold_updates=int(rep.threshold_updates))
+                     threshold_updates=int(rep.threshold_updates), waves=int(rep.waves),
+                     tile_pairs=int(rep.tile_pairs))
 
 
 def covariance(X, precision: str = "mixed", stream=None, workspace=None, out=None):
@@ -315,13 +327,47 @@ def autotune(X, stream=None, workspace=None):
     return (int(tr.value), int(tc.value)), {(64, 32): float(ms[0]), (32, 32): float(ms[1]), (64, 16): float(ms[2])}
 
 
+def autotune_batch(Xs, stream=None, workspace=None):
+    """lingam_autotune_batch on a list of datasets: times lingam_fit_batch with 64x32, 32x32
+    and 64x16 pair tiles, records the fastest for the bucket of the largest p and n;
+    returns ((rows, cols), {shape: ms})."""
+    L = load()
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    items = [_data_ptr(X) for X in Xs]
+    count = len(items)
+    o, _ = make_opts("mixed", items[0][3], stream=stream)
+    pa = (ctypes.c_longlong * count)(*[it[1] for it in items])
+    na = (ctypes.c_longlong * count)(*[it[2] for it in items])
+    need = int(L.lingam_workspace_size_batch(count, pa, na, ctypes.byref(o)))
+    if workspace is None or workspace.numel() < need:
+        workspace = alloc_workspace(need)
+    xp = (ctypes.c_void_p * count)(*[it[0] for it in items])
+    tr, tc = ctypes.c_int(0), ctypes.c_int(0)
+    ms = (ctypes.c_double * 3)()
+    st = L.lingam_autotune_batch(count, xp, pa, na, ctypes.c_void_p(workspace.data_ptr()), ctypes.byref(o),
+                                 ctypes.byref(tr), ctypes.byref(tc), ms)
+    del items
+    if st != LINGAM_OK:
+        raise LingamError(st, status_string(st))
+    return (int(tr.value), int(tc.value)), {(64, 32): float(ms[0]), (32, 32): float(ms[1]), (64, 16): float(ms[2])}
+
+
+def batch_tile_shape(maxp: int, maxn: int) -> tuple[int, int]:
+    """The pair-tile shape batch calls use for a batch whose largest problem is maxp x maxn."""
+    L = load()
+    return int(L.lingam_batch_tile_rows(maxp, maxn)), int(L.lingam_batch_tile_cols(maxp, maxn))
+
+
 def autotune_reset():
     load().lingam_autotune_reset()
 
 
 def selftest_wait(which: int, timeout_s: float) -> int:
     """lingam_selftest_wait: the status one device-side wait recorded after waiting for an
-    event that never happens (0: mbarrier phase, 1: grid barrier, 2: wave word)."""
+    event that never happens (0: mbarrier phase, 1: grid barrier, 2: wave word, 3: the B
+    fit's Cholesky row flag)."""
     obs = ctypes.c_int(0)
     st = load().lingam_selftest_wait(int(which), float(timeout_s), ctypes.byref(obs))
     if st != LINGAM_OK:
@@ -375,8 +421,9 @@ def batch_workspace(ps, ns, precision: str = "mixed", input_dtype=np.float32):
 
 
 def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = True, stream=None, workspace=None,
-              want_report: bool = False, want_scores: bool = False) -> BatchResult:
-    """lingam_fit_batch over a list of datasets (numpy or torch, each p_k x n_k, one dtype)."""
+              want_report: bool = False, want_scores: bool = False, tile_i: int = 0, tile_j: int = 0) -> BatchResult:
+    """lingam_fit_batch over a list of datasets (numpy or torch, each p_k x n_k, one dtype);
+    tile_i x tile_j: the pair-tile shape of the mixed path (0, 0: the batch autotuner's)."""
     L = load()
     torch = _torch()
     if stream is None:
@@ -385,7 +432,8 @@ def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = T
     count = len(items)
     if len({it[3] for it in items}) > 1:
         raise TypeError("all datasets of a batch must share one dtype")
-    o, _ = make_opts(precision, items[0][3] if items else np.float32, prune, True, 0, 10.0, stream)
+    o, _ = make_opts(precision, items[0][3] if items else np.float32, prune, True, 0, 10.0, stream,
+                     tile_i=tile_i, tile_j=tile_j)
     ps = [it[1] for it in items]
     ns = [it[2] for it in items]
     pa = (ctypes.c_longlong * count)(*ps)
@@ -416,8 +464,10 @@ def fit_batch(Xs, precision: str = "mixed", prune: bool = True, want_B: bool = T
 
 
 def fit_bootstrap(X, idx, precision: str = "mixed", prune: bool = True, want_B: bool = True, stream=None,
-                  workspace=None, want_report: bool = False, want_scores: bool = False) -> BatchResult:
-    """lingam_fit_bootstrap: X (p x n), idx (nboot x n column indices, numpy or CUDA tensor)."""
+                  workspace=None, want_report: bool = False, want_scores: bool = False, tile_i: int = 0,
+                  tile_j: int = 0) -> BatchResult:
+    """lingam_fit_bootstrap: X (p x n), idx (nboot x n column indices, numpy or CUDA tensor);
+    tile_i x tile_j as for fit_batch."""
     L = load()
     torch = _torch()
     if stream is None:
@@ -431,7 +481,7 @@ def fit_bootstrap(X, idx, precision: str = "mixed", prune: bool = True, want_B: 
         iptr, nboot = idx.data_ptr(), idx.shape[0]
     if idx.shape[1] != n:
         raise ValueError("idx must be nboot x n")
-    o, _ = make_opts(precision, dt, prune, True, 0, 10.0, stream)
+    o, _ = make_opts(precision, dt, prune, True, 0, 10.0, stream, tile_i=tile_i, tile_j=tile_j)
     need = int(L.lingam_workspace_size_bootstrap(p, n, nboot, ctypes.byref(o)))
     if need == 0:
         raise LingamError(LINGAM_EINVAL, "invalid sizes or options")

@@ -70,6 +70,10 @@ def test_tile_rows_default_rule(lib):
     assert lingam.tile_rows(1000, 10000) == 64
     assert lingam.tile_rows(0, 100) == 0
     assert lingam.tile_shape(1000, 10000) == (64, 32)
+    # batches: a table of their own, default 32 x 32
+    assert lingam.batch_tile_shape(50, 2000) == (32, 32)
+    assert lingam.batch_tile_shape(1000, 10000) == (32, 32)
+    assert lib.lingam_batch_tile_rows(0, 100) == 0
     o, _ = lingam.make_opts()
     for ti, tj in ((16, 0), (48, 0), (128, 0), (0, 8), (0, 64), (32, 16)):
         o.tile_i, o.tile_j = ti, tj

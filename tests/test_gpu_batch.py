@@ -130,22 +130,26 @@ def _hard_members(rng_seed):
     return [Xh.astype(np.float32), Xc.astype(np.float32)]
 
 
-def test_batch_matches_oracle():
-    """Batch members (uneven sizes plus a heavy-tailed and a near-collinear member) against
-    the oracle: every complete score, root score and margin bound of every iteration on the
-    common prefix within 1e-4, and the full order wherever every margin is resolved."""
-    sizes = [(5, 4000), (12, 3000), (20, 2000), (33, 2500)]
+@pytest.mark.parametrize("tile_i,tile_j", [(0, 0), (64, 32), (64, 16)])
+def test_batch_matches_oracle(tile_i, tile_j):
+    """Batch members (uneven sizes, one above 64 variables, plus a heavy-tailed and a
+    near-collinear member) against the oracle, with each pair-tile shape of the batch kernel
+    (0 x 0: the batch autotuner's default, 32 x 32): every complete score, root score and
+    margin bound of every iteration on the common prefix within 1e-4, and the full order
+    wherever every margin is resolved."""
+    sizes = [(5, 4000), (12, 3000), (20, 2000), (33, 2500), (70, 1500)]
     ds = []
     for k, (p, n) in enumerate(sizes):
         ds.append(synth.lingam_dataset(p, n, min(1.0, 4.0 / (p - 1)), seed=40 + k).X.astype(np.float32))
     ds += _hard_members(48)
-    res = lingam.fit_batch([_dev(X) for X in ds], precision="mixed", want_report=True, want_scores=True)
+    res = lingam.fit_batch([_dev(X) for X in ds], precision="mixed", want_report=True, want_scores=True,
+                           tile_i=tile_i, tile_j=tile_j)
     assert res.status == 0
     for m, (X32, o, B) in enumerate(zip(ds, res.orders, res.Bs)):
         o_order, o_B, o_S = oracle.fit(X32.astype(np.float64))
         k, worst = _member_vs_oracle(o, res.scores[m], res.root_scores[m], res.margins[m], o_order, o_S, atol=1e-4)
-        print(f"member {m} (p={X32.shape[0]}): order equals the oracle on {k} of {len(o)} iterations, "
-              f"max |dS| {worst:.2e} on the common prefix")
+        print(f"tiles {tile_i}x{tile_j} member {m} (p={X32.shape[0]}): order equals the oracle on {k} of {len(o)} "
+              f"iterations, max |dS| {worst:.2e} on the common prefix")
         if k == len(o):
             assert np.abs(B - o_B).max() <= 1e-4 * max(1.0, np.abs(o_B).max())
 
@@ -267,3 +271,25 @@ def test_batched_workload_full_size():
         single, roots, margins = _single(Xs[k])
         j = _agree_until_unresolved(ru.orders[k], single.order, roots, margins)
         print(f"uneven dataset {k} (p={Xs[k].shape[0]}): order equals the single fit on {j} iterations")
+
+
+def test_batch_autotuner_records_its_choice():
+    """lingam_autotune_batch times the three tile shapes on the caller's batch and records the
+    fastest for the bucket of the largest p and n; later calls with tile_i = tile_j = 0 use it
+    and give orders within the batch's own tolerance of an explicit-shape call."""
+    ds = synth.uneven_batch(12, seed=21)
+    Xs = [_dev(d.X[:, : min(d.X.shape[1], 2000)].astype(np.float32)) for d in ds]
+    maxp = max(x.shape[0] for x in Xs)
+    maxn = max(x.shape[1] for x in Xs)
+    lingam.autotune_reset()
+    assert lingam.batch_tile_shape(maxp, maxn) == (32, 32)
+    shape, ms = lingam.autotune_batch(Xs)
+    print(f"batch autotune (12 datasets, p <= {maxp}, n <= {maxn}): {ms} -> {shape}")
+    assert shape in ms and all(v > 0 for v in ms.values())
+    assert ms[shape] == min(ms.values())
+    assert lingam.batch_tile_shape(maxp, maxn) == shape
+    auto = lingam.fit_batch(Xs, precision="mixed")
+    expl = lingam.fit_batch(Xs, precision="mixed", tile_i=shape[0], tile_j=shape[1])
+    assert auto.status == 0 and all(np.array_equal(a, b) for a, b in zip(auto.orders, expl.orders))
+    lingam.autotune_reset()
+    assert lingam.batch_tile_shape(maxp, maxn) == (32, 32)
