@@ -567,6 +567,9 @@ def run_ours(args, rank: int, world: int):
     roofline["waves_per_step"] = int(rt.waves)
     roofline["tile_pairs_per_step"] = int(rt.tile_pairs)
     roofline["useful_fraction_of_tile_pairs"] = float(rt.pairs_total) / max(1, int(rt.tile_pairs))
+    waste = max(1, int(rt.tile_pairs) - int(rt.pairs_total))
+    roofline["tile_waste_shares"] = {"empty_columns": rt.empty_col_pairs / waste, "row_padding": rt.pad_row_pairs / waste,
+                                     "column_block_duplicates": 1.0 - (rt.empty_col_pairs + rt.pad_row_pairs) / waste}
 
     line = {"metric": METRIC if (p, n) == (P_DEFAULT, N_DEFAULT) else
             f"pair-sample evals/s (unpruned-equivalent) at p={p}, n={n}",

@@ -39,6 +39,13 @@
  *     them back into it) and the call returns after that stream has drained
  *     (it is synchronous).
  *   - The device is the CUDA device current on the calling thread.
+ *   - Environment variables, read by the library: LINGAM_LOG=1 prints one
+ *     line per call on stderr (entry point, sizes, status); LINGAM_FAULT=<step>
+ *     makes the named step of every call report a failed launch (host-side
+ *     fault injection for testing: standardize, covariance, iteration:<k>,
+ *     bfit, batch); LINGAM_NARROW=<rows> sets the fewest rows for which a wave
+ *     of 16 columns or fewer of a 64 x 32 single fit runs on 128 x 16 tiles
+ *     (default 256; 0 turns these narrow waves off, a switch for measurement).
  */
 #ifndef LINGAM_H
 #define LINGAM_H
@@ -148,6 +155,8 @@ typedef struct {
     long long tile_pairs;        /* pairs the waves' tiles computed: tiles x rows x columns, row
                                     padding, unused columns and the duplicate half of the
                                     columns' own block included (pairs_total are the useful ones) */
+    long long empty_col_pairs;   /* of tile_pairs: those in column slots a wave left empty */
+    long long pad_row_pairs;     /* of tile_pairs: those of the padding rows of a wave's last tile */
 } lingam_report;
 
 /* Fills *opts with the defaults: MIXED, F32, prune = reuse = 1, autotuned

@@ -88,6 +88,9 @@ struct Ctl {
     // waves run over the fit, and the pairs their tiles computed (tiles x rows x columns,
     // padding and the mirrored half of the column block included)
     long long waves, tile_pairs;
+    // of tile_pairs: pairs in column slots the wave left empty, and pairs of the padding rows
+    // of its last tile (the rest of the waste is the duplicate half of the columns' block)
+    long long empty_col_pairs, pad_row_pairs;
 };
 
 __host__ __device__ inline unsigned long long pack_wave(unsigned seq, int done, int ntiles, int ncol, int nrow) {
@@ -167,6 +170,8 @@ struct Fit {
     int maxsplit;        // sample splits at most
     int nslots;          // partial-moment slots (one per tile and CTA segment of a wave) the workspace holds
     int split_n;         // single fits: at most about split_n CTAs share a tile's samples (0 = as many as fill the grid)
+    int narrow;          // single fits on 64 x 32 tiles: waves of <= 16 columns and at least this many
+                         // rows run on 128 x 16 tiles (0: never)
     double gamma0;       // 0: prune against the lowest complete score; > 0: the paper's threshold
                          // schedule (Sec. III-B/C): threshold gamma0, times gamma_c while no variable
                          // can finish below it

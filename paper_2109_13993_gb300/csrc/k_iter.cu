@@ -87,6 +87,25 @@ using CfgF64 = PairShape<float, 64, 32, 512, kChunk, kChunk + 4, 3, 1>;      // 
 using CfgF32 = PairShape<float, 32, 32, 256, kChunk, kChunk + 4, 3, 2>;      // FP32, 32 x 32 tiles
 using CfgF16 = PairShape<float, 64, 16, 256, kChunk, kChunk + 4, 2, 2>;      // FP32, 64 x 16 tiles
 using CfgD = PairShape<double, 32, 32, 256, kChunk64, kChunk64 + 2, 3, 1>;   // FP64 path
+// The narrow waves of the 64 x 32 kernel: a wave with 16 columns or fewer (the last wave of
+// an iteration, when few candidates are left) runs on 128 x 16 tiles with the same 512
+// threads and copy ring (144 rows of 64-sample chunks in each of the three stages), so its
+// tiles hold the same 2048 pairs and twice the rows, instead of leaving half of the column
+// slots empty.
+using CfgN = PairShape<float, 128, 16, 512, kChunk / 2, kChunk / 2 + 4, 3, 1>;
+constexpr int kNarrowBaseRows = CfgF64::TI;   // the tile rows of the kernel's other waves
+
+static_assert(size_t(3) * (CfgN::TI + CfgN::TJ) * CfgN::LDS <= size_t(3) * (CfgF64::TI + CfgF64::TJ) * CfgF64::LDS,
+              "the narrow waves' ring fits in the 64 x 32 kernel's");
+
+// Rows of the tiles of a wave with ncol columns and nrow rows: narrow waves (ncol <= 16 and
+// nrow >= Fit::narrow > 0) have 128-row tiles, the others tile_rows.
+__host__ __device__ __forceinline__ bool wave_is_narrow(int narrow, int ncol, int nrow) {
+    return narrow > 0 && ncol <= CfgN::TJ && nrow >= narrow;
+}
+__host__ __device__ __forceinline__ int wave_tile_rows(int narrow, int ncol, int nrow, int tile_rows) {
+    return wave_is_narrow(narrow, ncol, nrow) ? CfgN::TI : tile_rows;
+}
 
 // The kernels' dynamic shared memory (copy ring, sort area, mbarriers).  Referenced by
 // name in the compute loop so that its loads are shared-memory loads with 32-bit
@@ -222,6 +241,33 @@ __device__ __forceinline__ void load16_cg(double* v, const double* src) {
     }
 }
 
+// gpu-scope release and acquire operations for the barrier and publication protocols: a
+// CTA barrier orders every thread's writes before thread 0's release, and thread 0's
+// acquire before every thread's later reads.
+__device__ __forceinline__ unsigned atom_add_release(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" : : "l"(p), "l"(v) : "memory");
+}
+
 // Grid-wide barrier, bounded: returns false when this CTA gave up (timeout, recorded)
 // or another CTA did (ctl->abort).  The arrival count only grows: it is zero when a
 // fit starts and every CTA of a launch arrives once per barrier, so the arrivals at a
@@ -234,14 +280,12 @@ __device__ bool grid_sync(Ctl* ctl, unsigned long long tmo) {
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned G = gridDim.x;
-        __threadfence();
-        const unsigned old = atomicAdd(&ctl->bar_count, 1u);
+        const unsigned old = atom_add_release(&ctl->bar_count, 1u);
         const unsigned target = old - old % G + G;
-        volatile unsigned* cntp = &ctl->bar_count;
         volatile int* abortp = &ctl->abort;
         unsigned long long t0 = 0;
         for (;;) {
-            const unsigned c = *cntp;
+            const unsigned c = ld_acquire(&ctl->bar_count);
             const int ab = *abortp;
             if (ab) {
                 ok = 0;
@@ -258,7 +302,6 @@ __device__ bool grid_sync(Ctl* ctl, unsigned long long tmo) {
                 break;
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -430,7 +473,8 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
             for (int c = 0; c < nc; ++c) f.cols[c] = sigma[c];
             ctl->ncol = nc;
             ctl->nrow = r;
-            ctl->ntiles = (r + TI - 1) / TI;
+            const int ti = wave_tile_rows(f.narrow, nc, r, TI);
+            ctl->ntiles = (r + ti - 1) / ti;
         }
     }
 }
@@ -780,7 +824,8 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
     }
     __syncthreads();   // every thread's writes precede the publication below
     if (tid == 0) {
-        const int ntiles_next = (nc + nr + TI - 1) / TI;
+        const int ti_next = wave_tile_rows(f.narrow, nc, nc + nr, f.narrow ? kNarrowBaseRows : TI);
+        const int ntiles_next = (nc + nr + ti_next - 1) / ti_next;
         if (nc == 0) {
             ctl->root = root;
             ctl->rm_root = root;
@@ -800,11 +845,11 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
         ctl->merged = 0;
         ctl->waves += 1;
         ctl->tile_pairs += (long long)ntiles * TI * TJ;
+        ctl->empty_col_pairs += (long long)(TJ - ncol) * ntiles * TI;
+        ctl->pad_row_pairs += (long long)(ntiles * TI - nrow) * ncol;
         if (seq != 0) {
             // publish: the CTAs of a single fit wait for this word instead of a grid barrier
-            __threadfence();
-            *reinterpret_cast<volatile unsigned long long*>(&ctl->wave_word) =
-                pack_wave(seq, nc == 0, nc == 0 ? 0 : ntiles_next, nc, nc + nr);
+            st_release64(&ctl->wave_word, pack_wave(seq, nc == 0, nc == 0 ? 0 : ntiles_next, nc, nc + nr));
         }
     }
 }
@@ -1328,18 +1373,13 @@ __device__ __noinline__ void merge_item(const Fit& f, const Wave& wv, const Span
             }
             f.colsum[(size_t(t) * PARTS + part) * TJ + cc] = cs;
         }
-        // the barrier orders every thread's rowsum and colsum stores before thread 0's fence,
-        // whose release covers them for the CTA that counts the last item
+        // the barrier orders every thread's rowsum and colsum stores before thread 0's
+        // acquire-release count, which makes them visible to the CTA that counts the last
+        // item (and the other items' stores to this CTA when it is that one)
         __syncthreads();
-        if (tid == 0) {
-            __threadfence();
-            sh.flag = (atomicAdd(&ctl->merged, 1) == ntiles * PARTS - 1);
-        }
+        if (tid == 0) sh.flag = (atom_add_acq_rel(&ctl->merged, 1) == ntiles * PARTS - 1);
         __syncthreads();
-        if (sh.flag) {
-            __threadfence();
-            wave_finalize<CONS, TI, TJ>(f, wv, it, sh.red, seq);
-        }
+        if (sh.flag) wave_finalize<CONS, TI, TJ>(f, wv, it, sh.red, seq);
         __syncthreads();
     }
 }
@@ -1610,6 +1650,28 @@ __device__ __noinline__ void iteration_tail(const Fit& f, int it, IterShared& sh
     }
 }
 
+// A narrow wave's compute phase, grid barrier and merge, out of line: the 64 x 32 kernel's
+// own sample loop stays the only one inlined into it (its speed depends on that).  Returns
+// false when the CTA must leave the kernel.
+template <class Cfg>
+__device__ __noinline__ bool narrow_wave(const Fit& f, Ctl* ctl, const Wave& wv, const Span& sp,
+                                         typename Cfg::T* ring, uint64_t* full, uint64_t* empty, IterShared& sh,
+                                         int& chunk_base, int it, unsigned seq, unsigned long long tmo, bool timed,
+                                         unsigned long long& tph) {
+    if (!compute_phase<Cfg>(f, ctl, wv, sp, ring, full, empty, sh, chunk_base)) {
+        ctl->abort = 1;
+        return false;
+    }
+    if (!grid_sync(ctl, tmo)) return false;
+    if (timed) {
+        const unsigned long long t = global_ns();
+        ctl->phase_ns[0] += t - tph;
+        tph = t;
+    }
+    merge_phase<Cfg>(f, wv, sp, it, sh, ring, seq);
+    return true;
+}
+
 // Wait (bounded) until the wave finalisation of a single fit has published wave word
 // seq; returns the next wave and whether the iteration is done.  Returns false when
 // this CTA gave up (timeout, recorded) or another CTA did.
@@ -1618,11 +1680,10 @@ __device__ bool wait_wave(Ctl* ctl, unsigned seq, unsigned long long tmo, Wave& 
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned long long* wp = &ctl->wave_word;
         volatile int* abortp = &ctl->abort;
         unsigned long long w = 0, t0 = 0;
         for (;;) {
-            w = *wp;
+            w = ld_acquire64(&ctl->wave_word);
             const int ab = *abortp;
             if (ab) {
                 ok = 0;
@@ -1639,7 +1700,6 @@ __device__ bool wait_wave(Ctl* ctl, unsigned seq, unsigned long long tmo, Wave& 
                 break;
             }
         }
-        __threadfence();
         s_word = w;
         s_ok = ok;
     }
@@ -1700,17 +1760,29 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_iteration(Fit f, int i
         const long long gcap = f.split_n > 0 ? min((long long)gridDim.x, (long long)wv.ntiles * f.split_n)
                                              : (long long)gridDim.x;
         const Span sp = single_span((long long)wv.ntiles * (f.ld / kSub), gcap);
-        if (!compute_phase<Cfg>(f, ctl, wv, sp, ring, full, empty, sh, chunk_base)) {
-            ctl->abort = 1;
-            return;
+        // a narrow wave (16 columns or fewer) of the 64 x 32 kernel runs on 128 x 16 tiles,
+        // compute and merge out of line
+        bool narrow = false;
+        if constexpr (std::is_same<Cfg, CfgF64>::value) narrow = wave_is_narrow(f.narrow, wv.ncol, wv.nrow);
+        if (narrow) {
+            if constexpr (std::is_same<Cfg, CfgF64>::value) {
+                if (!narrow_wave<CfgN>(f, ctl, wv, sp, reinterpret_cast<float*>(ring), full, empty, sh, chunk_base,
+                                       it, seq, tmo, timed, tph))
+                    return;
+            }
+        } else {
+            if (!compute_phase<Cfg>(f, ctl, wv, sp, ring, full, empty, sh, chunk_base)) {
+                ctl->abort = 1;
+                return;
+            }
+            if (!grid_sync(ctl, tmo)) return;
+            if (timed) {
+                const unsigned long long t = global_ns();
+                ctl->phase_ns[0] += t - tph;
+                tph = t;
+            }
+            merge_phase<Cfg>(f, wv, sp, it, sh, ring, seq);
         }
-        if (!grid_sync(ctl, tmo)) return;
-        if (timed) {
-            const unsigned long long t = global_ns();
-            ctl->phase_ns[0] += t - tph;
-            tph = t;
-        }
-        merge_phase<Cfg>(f, wv, sp, it, sh, ring, seq);
         fence_proxy_async();   // the merge used the copy ring as scratch
         // the wave's finalisation runs after every merge item, so its published word also
         // tells that every CTA is done with this wave's partial moments

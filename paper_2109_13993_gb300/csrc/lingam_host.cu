@@ -197,6 +197,17 @@ static EventPool* event_pool(int dev) {
 }
 
 // The device view of one problem laid out in `base` (a workspace region of layout L).
+// Narrow waves: waves of <= 16 columns and at least this many rows run on 128 x 16 tiles
+// (LINGAM_NARROW=<rows> overrides the default; 0 turns them off, a switch for measuring them).
+constexpr int kNarrowMinRows = 256;
+static int narrow_min_rows() {
+    static const int v = [] {
+        const char* e = std::getenv("LINGAM_NARROW");
+        return e && *e ? std::max(0, std::atoi(e)) : kNarrowMinRows;
+    }();
+    return v;
+}
+
 static Fit make_fit(char* base, const Layout& L, int p, int n, const lingam_opts& o, bool want_scores) {
     Fit f;
     std::memset(&f, 0, sizeof(f));
@@ -250,6 +261,7 @@ static Fit make_fit(char* base, const Layout& L, int p, int n, const lingam_opts
     const TileShape ts = o.precision == LINGAM_MIXED ? choose_tile(p, n, o.tile_i, o.tile_j) : TileShape{32, 32};
     f.tile_rows = ts.rows;
     f.tile_cols = ts.cols;
+    f.narrow = (o.precision == LINGAM_MIXED && ts.rows == 64 && ts.cols == 32) ? narrow_min_rows() : 0;
     return f;
 }
 
@@ -453,6 +465,8 @@ static int fit_one(const void* X, long long p_, long long n_, int* order, double
             rep->threshold_updates = ch.gsteps;
             rep->waves = ch.waves;
             rep->tile_pairs = ch.tile_pairs;
+            rep->empty_col_pairs = ch.empty_col_pairs;
+            rep->pad_row_pairs = ch.pad_row_pairs;
         }
         if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) status = LINGAM_ECUDA;
         if (rep && status == LINGAM_OK) {
@@ -776,6 +790,7 @@ static int fit_many(std::vector<BatchItem>& items, void* workspace, const lingam
         f.ctl = reinterpret_cast<Ctl*>(ws + BL.off_ctls) + k;
         f.tile_rows = ts.rows;
         f.tile_cols = ts.cols;
+        f.narrow = 0;   // the batch kernel runs every wave on the call's tile shape
         fits[size_t(k)] = f;
         SrcDesc sd;
         if (boot) {

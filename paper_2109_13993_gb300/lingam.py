@@ -42,7 +42,8 @@ class Report(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong), ("t_pair_iter_ms", _c_dbl_p),
                 ("t_compute_ms", ctypes.c_double), ("t_merge_ms", ctypes.c_double), ("t_remove_ms", ctypes.c_double),
                 ("threshold_updates", ctypes.c_longlong), ("waves", ctypes.c_longlong),
-                ("tile_pairs", ctypes.c_longlong)]
+                ("tile_pairs", ctypes.c_longlong), ("empty_col_pairs", ctypes.c_longlong),
+                ("pad_row_pairs", ctypes.c_longlong)]
 
 
 class LingamError(RuntimeError):
@@ -182,6 +183,8 @@ class FitResult:
     threshold_updates: int = 0
     waves: int = 0
     tile_pairs: int = 0
+    empty_col_pairs: int = 0
+    pad_row_pairs: int = 0
 
 
 def _torch():
@@ -266,7 +269,8 @@ def fit(X, precision: str = "mixed", prune: bool = True, reuse: bool = True, for
                      pairs_total=int(rep.pairs_total), pairs_unpruned=int(rep.pairs_unpruned),
                      kernel_launches=int(rep.kernel_launches), t_pair_iter_ms=tpi,
                      threshold_updates=int(rep.threshold_updates), waves=int(rep.waves),
-                     tile_pairs=int(rep.tile_pairs))
+                     tile_pairs=int(rep.tile_pairs), empty_col_pairs=int(rep.empty_col_pairs),
+                     pad_row_pairs=int(rep.pad_row_pairs))
 
 
 def covariance(X, precision: str = "mixed", stream=None, workspace=None, out=None):

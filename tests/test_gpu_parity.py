@@ -212,6 +212,57 @@ def test_split_n_matches_oracle_and_default(name, split_n):
     print(f"{name} split_n={split_n}: max score error {tau.max():.2e}")
 
 
+# ---------------------------------------------------------------- narrow waves (128 x 16 tiles)
+
+_NARROW_CHILD = r"""
+import json, sys, numpy as np, torch
+from paper_2109_13993_gb300 import lingam, synth
+d = synth.workload(sys.argv[1], seed=1)
+X = torch.tensor(d.X.astype(np.float32), device="cuda")
+order = np.array(json.loads(sys.argv[2]), dtype=np.int32)
+r = lingam.fit(X, prune=False, forced_order=order, want_scores=True)
+f = lingam.fit(X)
+np.save(sys.argv[3], r.scores)
+print("RESULT" + json.dumps({"order": f.order.tolist(), "tile_pairs": f.tile_pairs, "pairs": f.pairs_total}))
+"""
+
+
+def _narrow_run(name, order, narrow, out):
+    """A fit of workload `name` in a child process with LINGAM_NARROW=narrow: forced-order
+    scores (saved to `out`) and the free run's order and pair counts."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _NARROW_CHILD, name, json.dumps(order.tolist()), out],
+                       env=dict(os.environ, LINGAM_NARROW=str(narrow)), cwd=root, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("RESULT")][-1][len("RESULT"):])
+
+
+@pytest.mark.parametrize("name,narrow", [("p100_n10000", 1), ("p300_n5000", 1), ("p300_n5000", 256)])
+def test_narrow_waves_match_full_width_waves(name, narrow, tmp_path):
+    """Waves of 16 columns or fewer and at least LINGAM_NARROW rows run on 128 x 16 tiles
+    (default 256 rows; 0 turns them off).  With and without them the scores agree up to the
+    FP32 rounding of how each pair's samples were split over CTAs, both agree with the oracle
+    within 1e-4, the narrow tiles compute fewer pairs, and (at p = 100, where no iteration is
+    within FP32 rounding of a tie) the free-run orders and evaluated pairs are the same."""
+    d = synth.workload(name, seed=1)
+    X32 = d.X.astype(np.float32)
+    o_order, o_B, o_S = oracle.fit(X32.astype(np.float64))
+    on = _narrow_run(name, o_order, narrow, str(tmp_path / "on.npy"))
+    off = _narrow_run(name, o_order, 0, str(tmp_path / "off.npy"))
+    S_on, S_off = np.load(str(tmp_path / "on.npy")), np.load(str(tmp_path / "off.npy"))
+    _check_scores(S_on, S_off, rtol=1e-5, atol=1e-8)
+    _check_scores(S_on, o_S, rtol=0.0, atol=1e-4)
+    if name == "p100_n10000":
+        assert on["order"] == off["order"] and on["pairs"] == off["pairs"]
+    assert on["tile_pairs"] < off["tile_pairs"]
+    print(f"{name} narrow >= {narrow} rows: {on['tile_pairs']} tile pairs against {off['tile_pairs']} "
+          f"({on['pairs']} useful)")
+
+
 # ---------------------------------------------------------------- worked example of the paper
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
