@@ -112,6 +112,7 @@ struct SrcDesc {
 struct Fit {
     int p;               // variables
     int n;               // samples
+    double inv_n;        // 1 / n (FP64 divisions are slow on this part; the removal multiplies)
     int ld;              // padded row length (multiple of kSampleAlign)
     int precision;       // LINGAM_MIXED or LINGAM_FP64
     int prune;           // threshold pruning on
@@ -314,6 +315,21 @@ __host__ __device__ inline float4 var_stats(double L, double Gs, int n, int ld) 
     const float off = float(-double(kSub) * (kLn2 + m));
     const double eps = double(off) + double(kSub) * (kLn2 + m);
     const double corr = (m * double(ld - n) - double(ld / kSub) * eps) / double(n);
+    return make_float4(float(corr), float(2.0 * (m - kBeta)), float(g), off);
+}
+
+// The same two from the removal's sums, with 1/n given (products instead of FP64 divisions,
+// which are slow on this part).
+__host__ __device__ __forceinline__ double hterm_inv(double lcc, double g, double inv_n) {
+    const double a = lcc * inv_n, b = g * inv_n;
+    return -kK1 * a * a - kK2 * b * b;
+}
+__host__ __device__ inline float4 var_stats_inv(double L, double Gs, int n, int ld, double inv_n) {
+    const double m = kBeta + L * inv_n;
+    const double g = Gs * inv_n;
+    const float off = float(-double(kSub) * (kLn2 + m));
+    const double eps = double(off) + double(kSub) * (kLn2 + m);
+    const double corr = (m * double(ld - n) - double(ld / kSub) * eps) * inv_n;
     return make_float4(float(corr), float(2.0 * (m - kBeta)), float(g), off);
 }
 

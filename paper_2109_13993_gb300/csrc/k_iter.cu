@@ -1561,9 +1561,7 @@ __device__ __noinline__ void remove_staged(const Fit& f, int vb, int vG, int r, 
             const float cc = float(c), ii = float(inv);
             float4* xw4 = reinterpret_cast<float4*>(xw);
             const float4* xr4 = reinterpret_cast<const float4*>(xr);
-#pragma unroll 4
-            for (int t4 = tid; t4 < ld / 4; t4 += NTH) {
-                const float4 a = xw4[t4], rr = xr4[t4];
+            auto update4 = [&](int t4, float4 a, float4 rr) {
                 float4 o;
                 o.x = fmaf(-cc, rr.x, a.x) * ii;
                 o.y = fmaf(-cc, rr.y, a.y) * ii;
@@ -1575,6 +1573,29 @@ __device__ __noinline__ void remove_staged(const Fit& f, int vb, int vG, int r, 
                 if (t + 1 < f.n) mom_add(o.y, lcc, g);
                 if (t + 2 < f.n) mom_add(o.z, lcc, g);
                 if (t + 3 < f.n) mom_add(o.w, lcc, g);
+            };
+            const int n4 = ld / 4;
+            constexpr int kPer = 8;
+            if (n4 <= NTH * kPer) {
+                // the thread's whole share of the row loaded first, all in flight together
+                // (the stores below could alias the loads, so they would not be hoisted)
+                float4 a[kPer], rr[kPer];
+#pragma unroll
+                for (int q = 0; q < kPer; ++q) {
+                    const int t4 = tid + q * NTH;
+                    if (t4 < n4) {
+                        a[q] = xw4[t4];
+                        rr[q] = xr4[t4];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kPer; ++q) {
+                    const int t4 = tid + q * NTH;
+                    if (t4 < n4) update4(t4, a[q], rr[q]);
+                }
+            } else {
+#pragma unroll 4
+                for (int t4 = tid; t4 < n4; t4 += NTH) update4(t4, xw4[t4], xr4[t4]);
             }
         } else {
             for (int t = tid; t < ld; t += NTH) {
@@ -1594,30 +1615,51 @@ __device__ __noinline__ void remove_staged(const Fit& f, int vb, int vG, int r, 
         }
     }
     __syncthreads();
-    for (int m = tid; m < nmine; m += NTH) {
+    // each row's warp sums in a warp tree, one warp per row (FP64 adds have a long latency
+    // on this part, so the chains are kept short)
+    const double inv_n = f.inv_n;
+    for (int m = wid; m < nmine; m += NW) {
         const int w = s_j[vb + m * vG];
         if (w == root) continue;
-        double L = 0.0, Gs = 0.0;
-        for (int k2 = 0; k2 < NW; ++k2) {
-            L += s_hp[size_t(m) * 2 * NW + k2];
-            Gs += s_hp[size_t(m) * 2 * NW + NW + k2];
+        double L = lane < NW ? s_hp[size_t(m) * 2 * NW + lane] : 0.0;
+        double Gs = lane < NW ? s_hp[size_t(m) * 2 * NW + NW + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            L += __shfl_xor_sync(0xffffffffu, L, o);
+            Gs += __shfl_xor_sync(0xffffffffu, Gs, o);
         }
-        f.hx[w] = hterm(L, Gs, double(f.n));
-        f.vstat[w] = var_stats(L, Gs, f.n, f.ld);
+        if (lane == 0) {
+            f.hx[w] = hterm_inv(L, Gs, inv_n);
+            f.vstat[w] = var_stats_inv(L, Gs, f.n, f.ld, inv_n);
+        }
     }
-    // UpdateCovMat (Algorithm 8 / Eq. CovUpdate), FP64, one read-modify-write per element
-    const long long total = (long long)nmine * r;
-#pragma unroll 4
-    for (long long idx = tid; idx < total; idx += NTH) {
-        const int m = int(idx / r), jj = int(idx - (long long)m * r);
+    // UpdateCovMat (Algorithm 8 / Eq. CovUpdate), FP64.  Sigma stays symmetric, so each
+    // unordered pair of U is updated once, by the CTA holding the row of its lower candidate
+    // position, which writes both of its elements (and both of the FP32 view's); a CTA reads
+    // only elements it writes itself.  Half the FP64 work of a full update, which the FP64
+    // rate of this part bounds.
+    for (int m = 0; m < nmine; ++m) {
         const int kk = vb + m * vG;
         const int w = s_j[kk];
-        const int j = s_j[jj];
-        if (w == root || j == root) continue;
+        if (w == root) continue;
+        const double aw = s_rj[kk], bw = s_ij[kk];
         double* row = f.sig + size_t(w) * p;
-        const double nv = (j == w) ? 1.0 : (row[j] - s_rj[kk] * s_rj[jj]) * (s_ij[kk] * s_ij[jj]);
-        row[j] = nv;
-        if constexpr (std::is_same<T, float>::value) f.sigf[size_t(w) * p + j] = sig_pair_f(nv);
+        if (tid == 0) {
+            row[w] = 1.0;
+            if constexpr (std::is_same<T, float>::value) f.sigf[size_t(w) * p + w] = sig_pair_f(1.0);
+        }
+        for (int jj = kk + 1 + tid; jj < r; jj += NTH) {
+            const int j = s_j[jj];
+            if (j == root) continue;
+            const double nv = (row[j] - aw * s_rj[jj]) * (bw * s_ij[jj]);
+            row[j] = nv;
+            f.sig[size_t(j) * p + w] = nv;
+            if constexpr (std::is_same<T, float>::value) {
+                const float2 fv = sig_pair_f(nv);
+                f.sigf[size_t(w) * p + j] = fv;
+                f.sigf[size_t(j) * p + w] = fv;
+            }
+        }
     }
     __syncthreads();
     fence_proxy_async();   // the copy ring is written by bulk copies later

@@ -213,6 +213,7 @@ static Fit make_fit(char* base, const Layout& L, int p, int n, const lingam_opts
     std::memset(&f, 0, sizeof(f));
     f.p = p;
     f.n = n;
+    f.inv_n = 1.0 / double(n);
     f.ld = L.ld;
     f.precision = o.precision;
     f.prune = o.prune;
