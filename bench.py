@@ -45,7 +45,7 @@ L2_FLUSH_BYTES = 256 << 20
 SFU_CLK_PER_PAIR_SAMPLE = 4.0 / 32.0 + (2.0 / 32.0) / 16.0
 # DRAM bytes (read + write) per launch of the iteration kernel, from an ncu capture of
 # the current kernel version (profiles/); None until the current version is captured.
-ITER_TRAFFIC_BYTES = 70.0e6   # ncu dram__bytes_read.sum + dram__bytes_write.sum, iteration 2 (55.9 + 14.1 MB)
+ITER_TRAFFIC_BYTES = 71.6e6   # ncu dram__bytes_read.sum + dram__bytes_write.sum, iteration 2 (55.1 + 16.5 MB)
 
 
 def unpruned_pair_samples(p: int, n: int) -> float:
