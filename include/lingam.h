@@ -79,8 +79,9 @@ typedef struct {
     int prune;               /* 1 = threshold pruning (Sec. III-B), 0 = compare every pair */
     int reuse;               /* 1 = one evaluation per unordered pair (Sec. III-A), 0 = every ordered pair */
     int tile_i, tile_j;      /* pair-tile shape of the mixed path, rows x columns: 64 x 32, 32 x 32 or
-                                64 x 16 (a zero in one takes 64 rows or 32 columns); both 0 = the
-                                autotuner's table (lingam_tile_rows/_cols).  The FP64 path uses 32 x 32. */
+                                64 x 16, and 32 x 16 for batch calls only (a zero in one takes 64 rows
+                                or 32 columns); both 0 = the autotuner's table (lingam_tile_rows/_cols,
+                                lingam_batch_tile_rows/_cols).  The FP64 path uses 32 x 32. */
     int split_n;             /* single fits: split of the sample axis.  0 (default) = stream-K over
                                 (tile, 32-sample group) units: a wave's units are spread over the whole
                                 grid, so a tile's samples are cut into as many CTA segments as it takes
@@ -229,10 +230,13 @@ int lingam_covariance(const void* X, long long p, long long n, double* Sigma, vo
  *                       lingam_fit_batch with opts on the mixed path, B not fitted) with
  *                       each shape: a warm-up call, the call that captures the graph, and
  *                       the timed third call (host wall time of the synchronous call).
- *                       Records the fastest for the bucket of the batch's largest p and n,
- *                       returns it in *tile_rows, *tile_cols, and ms[0..2] as for
- *                       lingam_autotune.  Costs nine batch calls; the workspace is as for
- *                       lingam_fit_batch.  LINGAM_EINVAL for the FP64 path.
+ *                       Batches have a fourth shape, 32 x 16 (128 threads, three CTAs
+ *                       per SM, 64-sample chunks), for many small problems.  Records the
+ *                       fastest for the bucket of the batch's largest p and n, returns it
+ *                       in *tile_rows, *tile_cols, and ms[0..3] (if not NULL) receive the
+ *                       times with 64 x 32, 32 x 32, 64 x 16 and 32 x 16 tiles.  Costs
+ *                       twelve batch calls; the workspace is as for lingam_fit_batch.
+ *                       LINGAM_EINVAL for the FP64 path.
  * lingam_autotune_reset -- forgets every measured choice (both tables).
  * The tables are shared by all threads of the process (guarded by a mutex).
  */
@@ -281,8 +285,8 @@ size_t lingam_workspace_size_batch(int count, const long long* p, const long lon
  * and replayed by every later such call; calls on the legacy default stream (NULL)
  * run without a graph.  opts->forced_order and opts->prior must be NULL, and
  * opts->max_iters and opts->gamma0 0; opts->split_n is ignored.  Pair tiles: on the
- * mixed path opts->tile_i x opts->tile_j for every problem of the call (64 x 32, 32 x 32
- * or 64 x 16), or, with both 0, the batch autotuner's shape for the largest p and n
+ * mixed path opts->tile_i x opts->tile_j for every problem of the call (64 x 32, 32 x 32,
+ * 64 x 16 or 32 x 16), or, with both 0, the batch autotuner's shape for the largest p and n
  * (lingam_batch_tile_rows/_cols); 32 x 32 on the FP64 path.
  */
 int lingam_fit_batch(int count, const void* const* X, const long long* p, const long long* n, int* const* order,

@@ -140,17 +140,60 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_coop(Fit f) {
 
 // Column j of R^{-1} by forward substitution (one CTA per column):
 //   y_k = ([k == j] - sum_{m<k} R[k][m] y_m) / R[k][k],  k = j..p-1.
-__global__ void k_tri_inv(Fit f) {
-    extern __shared__ double acc[];
+// For p <= NT kTriPer, thread t owns the entries i = t, t + NT, ... of the running sums, in
+// registers; column k + 1 of R is loaded while step k runs, so a step's critical path is one
+// barrier, a shared-memory read and a few FMAs; and the diagonal's reciprocals are formed
+// first, all at once (FP64 divisions are slow on this part).  Larger p: the plain loop.
+constexpr int kTriThreads = 256;
+constexpr int kTriPer = 4;
+__global__ void __launch_bounds__(kTriThreads) k_tri_inv(Fit f) {
+    extern __shared__ double sm_tri[];
+    double* acc = sm_tri;        // [p] running sums (entries of other threads read at step k)
     const int p = f.p, j = blockIdx.x, tid = threadIdx.x;
-    for (int i = tid; i < p; i += blockDim.x) acc[i] = 0.0;
-    __syncthreads();
-    for (int k = j; k < p; ++k) {
-        const double* rk = f.rmat + size_t(k) * p;   // column k of R: rk[i] = R[i][k]
-        const double y = ((k == j ? 1.0 : 0.0) - acc[k]) / rk[k];
-        if (tid == 0) f.rinv[size_t(k) * p + j] = y;
-        for (int i = k + 1 + tid; i < p; i += blockDim.x) acc[i] = fma(rk[i], y, acc[i]);
+    for (int i = tid; i < p; i += kTriThreads) acc[i] = 0.0;
+    if (p <= kTriThreads * kTriPer) {
+        double* invd = sm_tri + p;   // [p] 1 / R[k][k]
+        for (int i = tid; i < p; i += kTriThreads) invd[i] = i >= j ? 1.0 / f.rmat[size_t(i) * p + i] : 0.0;
         __syncthreads();
+        double a[kTriPer], cur[kTriPer];
+#pragma unroll
+        for (int q = 0; q < kTriPer; ++q) {
+            a[q] = 0.0;
+            const int i = tid + q * kTriThreads;
+            cur[q] = i < p ? f.rmat[size_t(j) * p + i] : 0.0;
+        }
+        for (int k = j; k < p; ++k) {
+            double nxt[kTriPer];
+            if (k + 1 < p) {
+#pragma unroll
+                for (int q = 0; q < kTriPer; ++q) {
+                    const int i = tid + q * kTriThreads;
+                    nxt[q] = i < p ? __ldg(f.rmat + size_t(k + 1) * p + i) : 0.0;
+                }
+            }
+            const double y = ((k == j ? 1.0 : 0.0) - acc[k]) * invd[k];
+            if (tid == 0) f.rinv[size_t(k) * p + j] = y;
+#pragma unroll
+            for (int q = 0; q < kTriPer; ++q) {
+                const int i = tid + q * kTriThreads;
+                if (i > k && i < p) {
+                    a[q] = fma(cur[q], y, a[q]);
+                    if (i == k + 1) acc[i] = a[q];   // the only sum step k + 1 reads
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < kTriPer; ++q) cur[q] = nxt[q];
+        }
+    } else {
+        __syncthreads();
+        for (int k = j; k < p; ++k) {
+            const double* rk = f.rmat + size_t(k) * p;   // column k of R: rk[i] = R[i][k]
+            const double y = ((k == j ? 1.0 : 0.0) - acc[k]) / rk[k];
+            if (tid == 0) f.rinv[size_t(k) * p + j] = y;
+            for (int i = k + 1 + tid; i < p; i += kTriThreads) acc[i] = fma(rk[i], y, acc[i]);
+            __syncthreads();
+        }
     }
 }
 
@@ -263,10 +306,10 @@ cudaError_t launch_fit_B(const Fit& f, cudaStream_t st) {
         cfg.numAttrs = 1;
         if ((e = cudaLaunchKernelEx(&cfg, k_chol_coop, f)) != cudaSuccess) return e;
     }
-    const size_t smem = size_t(p) * sizeof(double);
+    const size_t smem = (p <= kTriThreads * kTriPer ? 2 : 1) * size_t(p) * sizeof(double);
     e = ensure_smem_attr(reinterpret_cast<const void*>(k_tri_inv), smem);
     if (e != cudaSuccess) return e;
-    k_tri_inv<<<p, 256, smem, st>>>(f);
+    k_tri_inv<<<p, kTriThreads, smem, st>>>(f);
     k_B_out<<<g2, 256, 0, st>>>(f);
     return cudaGetLastError();
 }

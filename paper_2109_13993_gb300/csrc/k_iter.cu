@@ -94,6 +94,10 @@ using CfgD = PairShape<double, 32, 32, 256, kChunk64, kChunk64 + 2, 3, 1>;   // 
 // slots empty.
 using CfgN = PairShape<float, 128, 16, 512, kChunk / 2, kChunk / 2 + 4, 3, 1>;
 constexpr int kNarrowBaseRows = CfgF64::TI;   // the tile rows of the kernel's other waves
+// Batches of small problems: 32 x 16 tiles of 128 threads, 64-sample chunks, three CTAs per SM
+// (a problem's late iterations, with fewer than 32 variables left, fill half the rows of a
+// 64-row tile).  Batch kernel only.
+using CfgB = PairShape<float, 32, 16, 128, kChunk / 2, kChunk / 2 + 4, 3, 3>;
 
 static_assert(size_t(3) * (CfgN::TI + CfgN::TJ) * CfgN::LDS <= size_t(3) * (CfgF64::TI + CfgF64::TJ) * CfgF64::LDS,
               "the narrow waves' ring fits in the 64 x 32 kernel's");
@@ -113,6 +117,13 @@ __host__ __device__ __forceinline__ int wave_tile_rows(int narrow, int ncol, int
 extern __shared__ __align__(128) unsigned char smem_dyn[];
 
 constexpr int kSortMax = 8192;   // candidate sort in shared memory up to this many variables
+// The candidate sort's capacity of a kernel shape: the 32 x 16 batch shape keeps its shared
+// memory small (three CTAs per SM), so it sorts up to 2048 candidates (larger problems keep
+// index order: pruning efficiency only).
+template <class Cfg>
+__host__ __device__ constexpr int sort_max() {
+    return std::is_same<Cfg, CfgB>::value ? 2048 : kSortMax;
+}
 
 template <class Cfg>
 __host__ __device__ constexpr size_t stage_elems() {
@@ -125,7 +136,7 @@ __host__ __device__ constexpr size_t ring_bytes() {
 template <class Cfg>
 size_t iter_smem_bytes() {
     const size_t ring = ring_bytes<Cfg>();
-    const size_t sort = size_t(kSortMax) * sizeof(unsigned long long);
+    const size_t sort = size_t(sort_max<Cfg>()) * sizeof(unsigned long long);
     return (ring > sort ? ring : sort) + 2 * kStages * sizeof(uint64_t);   // full and empty barriers
 }
 
@@ -342,7 +353,7 @@ __device__ __forceinline__ int cta_of_unit(long long v, long long U, long long G
 }
 
 // ------------------------------------------------------------------ plan (CTA 0)
-template <int NTH, int TI, int TJ>
+template <int NTH, int TI, int TJ, int SORTMAX = kSortMax>
 __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* smem, int* red, int* sigma) {
     Ctl* ctl = f.ctl;
     const int p = f.p, tid = threadIdx.x;
@@ -358,8 +369,8 @@ __device__ __noinline__ void plan_phase(const Fit& f, int it, unsigned char* sme
     }
     // Sort by key: the order-preserving bits of the float score above the variable
     // index (ties by index).  Bitonic; compare-exchange stages with strides below 32
-    // run in registers.  Beyond kSortMax variables sigma stays in index order.
-    if (r <= kSortMax && r > 1) {
+    // run in registers.  Beyond SORTMAX variables sigma stays in index order.
+    if (r <= SORTMAX && r > 1) {
         int N = 32;
         while (N < r) N <<= 1;
         unsigned long long* key = reinterpret_cast<unsigned long long*>(smem);
@@ -840,17 +851,20 @@ __device__ __noinline__ void wave_finalize(const Fit& f, const Wave& wv, int it,
             ctl->ncol = nc;
             ctl->nrow = nc + nr;
             ctl->ntiles = ntiles_next;
-            ctl->wave += 1;
         }
         ctl->merged = 0;
-        ctl->waves += 1;
-        ctl->tile_pairs += (long long)ntiles * TI * TJ;
-        ctl->empty_col_pairs += (long long)(TJ - ncol) * ntiles * TI;
-        ctl->pad_row_pairs += (long long)(ntiles * TI - nrow) * ncol;
         if (seq != 0) {
             // publish: the CTAs of a single fit wait for this word instead of a grid barrier
             st_release64(&ctl->wave_word, pack_wave(seq, nc == 0, nc == 0 ? 0 : ntiles_next, nc, nc + nr));
         }
+        // the tile counters (read by the host after the call) as atomic additions after the
+        // publication, off the waves' critical path
+        atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->waves), 1ull);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->tile_pairs), (unsigned long long)ntiles * TI * TJ);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->empty_col_pairs),
+                  (unsigned long long)(TJ - ncol) * ntiles * TI);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->pad_row_pairs),
+                  (unsigned long long)(ntiles * TI - nrow) * ncol);
     }
 }
 
@@ -2222,7 +2236,8 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
     using T = typename Cfg::T;
     constexpr int CONS = Cfg::CONS, TI = Cfg::TI;
     T* ring = reinterpret_cast<T*>(smem_raw);
-    const size_t ring_or_sort = ring_bytes<Cfg>() > size_t(kSortMax) * 8 ? ring_bytes<Cfg>() : size_t(kSortMax) * 8;
+    const size_t ring_or_sort =
+        ring_bytes<Cfg>() > size_t(sort_max<Cfg>()) * 8 ? ring_bytes<Cfg>() : size_t(sort_max<Cfg>()) * 8;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + ring_or_sort);
     uint64_t* empty = full + kStages;
     volatile Ctl* vb = bctl;
@@ -2242,7 +2257,7 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
         // plan (a problem whose status turned bad stays done: it is not planned again)
         batch_active(fits, count, it, 0, bs);
         for (int d = blockIdx.x; d < count; d += gridDim.x)
-            if (bs.act[d]) plan_phase<CONS, TI, Cfg::TJ>(fits[d], it, smem_raw, sh.red, fits[d].sigma);
+            if (bs.act[d]) plan_phase<CONS, TI, Cfg::TJ, sort_max<Cfg>()>(fits[d], it, smem_raw, sh.red, fits[d].sigma);
         if (!grid_sync(bctl, tmo)) return;
         for (;;) {
             long long utot;
@@ -2354,6 +2369,7 @@ cudaError_t launch_batch(const Fit* fits_dev, int count, int maxp, int precision
     if (tile_rows == 64 && tile_cols == 32) return launch_batch_cfg<CfgF64>(fits_dev, count, maxp, bctl, nsm, st);
     if (tile_rows == 64 && tile_cols == 16) return launch_batch_cfg<CfgF16>(fits_dev, count, maxp, bctl, nsm, st);
     if (tile_rows == 32 && tile_cols == 32) return launch_batch_cfg<CfgF32>(fits_dev, count, maxp, bctl, nsm, st);
+    if (tile_rows == 32 && tile_cols == 16) return launch_batch_cfg<CfgB>(fits_dev, count, maxp, bctl, nsm, st);
     return cudaErrorInvalidValue;
 }
 

@@ -148,7 +148,7 @@ static bool valid_opts(const lingam_opts& o) {
     return (o.precision == LINGAM_MIXED || o.precision == LINGAM_FP64) &&
            (o.input_dtype == LINGAM_F32 || o.input_dtype == LINGAM_F64) && (o.prune == 0 || o.prune == 1) &&
            (o.reuse == 0 || o.reuse == 1) && o.split_n >= 0 && (o.tile_i == 0 || o.tile_i == 32 || o.tile_i == 64) &&
-           (o.tile_j == 0 || o.tile_j == 16 || o.tile_j == 32) && !(o.tile_i == 32 && o.tile_j == 16) &&
+           (o.tile_j == 0 || o.tile_j == 16 || o.tile_j == 32) &&
            std::isfinite(o.gamma0) && o.gamma0 >= 0.0 &&
            (o.gamma0 == 0.0 || (o.prune == 1 && o.reuse == 1 && std::isfinite(o.gamma_c) && o.gamma_c > 1.0));
 }
@@ -160,6 +160,9 @@ static TileShape batch_tile_shape(const lingam_opts& o, long long maxp, long lon
     if (o.tile_i != 0 || o.tile_j != 0) return TileShape{o.tile_i ? o.tile_i : 64, o.tile_j ? o.tile_j : 32};
     return autotune_batch_shape(maxp, maxn);
 }
+
+// Single fits run 64 x 32, 32 x 32 or 64 x 16 tiles (32 x 16 tiles are a batch shape).
+static bool single_fit_shape(const lingam_opts& o) { return !(o.tile_i == 32 && o.tile_j == 16); }
 
 static bool is_device_ptr(const void* ptr) {
     cudaPointerAttributes a;
@@ -291,7 +294,8 @@ static bool check_prior(const signed char* prior, int p, std::vector<int>& anc) 
 // cov_out != nullptr: stop after CalculateCovMat and copy Sigma (p x p) there.
 static int fit_one(const void* X, long long p_, long long n_, int* order, double* B, void* workspace,
                    const lingam_opts& o, lingam_report* rep, double* cov_out = nullptr) {
-    if (!X || !(order || cov_out) || !workspace || p_ < 1 || n_ < 3 || p_ > kMaxP || n_ > (1ll << 30) || !valid_opts(o))
+    if (!X || !(order || cov_out) || !workspace || p_ < 1 || n_ < 3 || p_ > kMaxP || n_ > (1ll << 30) || !valid_opts(o) ||
+        !single_fit_shape(o))
         return LINGAM_EINVAL;
     const int p = int(p_), n = int(n_);
     if (o.forced_order) {   // must be a permutation of 0..p-1
@@ -960,7 +964,7 @@ size_t lingam_workspace_size(long long p, long long n, const lingam_opts* opts) 
     lingam_opts o;
     lingam_default_opts(&o);
     if (opts) o = *opts;
-    if (p < 1 || n < 3 || p > kMaxP || n > (1ll << 30) || !valid_opts(o)) return 0;
+    if (p < 1 || n < 3 || p > kMaxP || n > (1ll << 30) || !valid_opts(o) || !single_fit_shape(o)) return 0;
     return make_layout(p, n, o.precision, o.input_dtype, o.prior != nullptr).total;
 }
 
@@ -1050,10 +1054,10 @@ int lingam_autotune_batch(int count, const void* const* X, const long long* p, c
         ord[size_t(k)].resize(size_t(p[k]));
         op[size_t(k)] = ord[size_t(k)].data();
     }
-    const TileShape cand[3] = {{64, 32}, {32, 32}, {64, 16}};
-    double t[3] = {0.0, 0.0, 0.0};
+    const TileShape cand[4] = {{64, 32}, {32, 32}, {64, 16}, {32, 16}};
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
     int best = 0;
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 4; ++c) {
         lingam_opts oc = o;
         oc.tile_i = cand[c].rows;
         oc.tile_j = cand[c].cols;
@@ -1072,7 +1076,7 @@ int lingam_autotune_batch(int count, const void* const* X, const long long* p, c
     *tile_rows = cand[best].rows;
     *tile_cols = cand[best].cols;
     if (ms)
-        for (int c = 0; c < 3; ++c) ms[c] = t[c];
+        for (int c = 0; c < 4; ++c) ms[c] = t[c];
     return LINGAM_OK;
 }
 

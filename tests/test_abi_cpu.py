@@ -81,6 +81,12 @@ def test_tile_rows_default_rule(lib):
     for ti, tj in ((64, 32), (32, 32), (64, 16), (0, 16), (32, 0)):
         o.tile_i, o.tile_j = ti, tj
         assert lib.lingam_workspace_size(10, 100, ctypes.byref(o)) > 0
+    # 32 x 16 tiles are a batch shape: batch sizing accepts them, single fits do not
+    o.tile_i, o.tile_j = 32, 16
+    ps = (ctypes.c_longlong * 1)(10)
+    ns = (ctypes.c_longlong * 1)(100)
+    assert lib.lingam_workspace_size_batch(1, ps, ns, ctypes.byref(o)) > 0
+    assert lib.lingam_workspace_size(10, 100, ctypes.byref(o)) == 0
 
 
 def test_batch_and_bootstrap_workspace_sizes(lib):
