@@ -226,7 +226,7 @@ def batched_workload(lingam, synth, torch, dev, stream, reps: int = 5) -> dict:
     # for each set's size bucket (the gathered resamples stand in for the bootstrap call)
     Xb = [X[:, idx[b].long()].contiguous() for b in range(idx.shape[0])]
     shapes_ms = {"bootstrap_256": {}, "uneven_64": {}}
-    for ti, tj in ((64, 32), (32, 32), (64, 16), (32, 16)):
+    for ti, tj in ((64, 32), (32, 32), (64, 16), (32, 16), (1, 1)):
         shapes_ms["bootstrap_256"][f"{ti}x{tj}"] = timed(
             lambda: lingam.fit_bootstrap(X, idx, workspace=wsb, tile_i=ti, tile_j=tj))
         shapes_ms["uneven_64"][f"{ti}x{tj}"] = timed(lambda: lingam.fit_batch(Xs, workspace=wsu, tile_i=ti, tile_j=tj))

@@ -79,9 +79,10 @@ typedef struct {
     int prune;               /* 1 = threshold pruning (Sec. III-B), 0 = compare every pair */
     int reuse;               /* 1 = one evaluation per unordered pair (Sec. III-A), 0 = every ordered pair */
     int tile_i, tile_j;      /* pair-tile shape of the mixed path, rows x columns: 64 x 32, 32 x 32 or
-                                64 x 16, and 32 x 16 for batch calls only (a zero in one takes 64 rows
-                                or 32 columns); both 0 = the autotuner's table (lingam_tile_rows/_cols,
-                                lingam_batch_tile_rows/_cols).  The FP64 path uses 32 x 32. */
+                                64 x 16, and for batch calls only 32 x 16 and 1 x 1 (one pair per warp)
+                                (a zero in one takes 64 rows or 32 columns); both 0 = the autotuner's
+                                table (lingam_tile_rows/_cols, lingam_batch_tile_rows/_cols).  The FP64
+                                path uses 32 x 32. */
     int split_n;             /* single fits: split of the sample axis.  0 (default) = stream-K over
                                 (tile, 32-sample group) units: a wave's units are spread over the whole
                                 grid, so a tile's samples are cut into as many CTA segments as it takes
@@ -230,13 +231,16 @@ int lingam_covariance(const void* X, long long p, long long n, double* Sigma, vo
  *                       lingam_fit_batch with opts on the mixed path, B not fitted) with
  *                       each shape: a warm-up call, the call that captures the graph, and
  *                       the timed third call (host wall time of the synchronous call).
- *                       Batches have a fourth shape, 32 x 16 (128 threads, three CTAs
- *                       per SM, 64-sample chunks), for many small problems.  Records the
- *                       fastest for the bucket of the batch's largest p and n, returns it
- *                       in *tile_rows, *tile_cols, and ms[0..3] (if not NULL) receive the
- *                       times with 64 x 32, 32 x 32, 64 x 16 and 32 x 16 tiles.  Costs
- *                       twelve batch calls; the workspace is as for lingam_fit_batch.
- *                       LINGAM_EINVAL for the FP64 path.
+ *                       Batches have two more shapes for many small problems: 32 x 16
+ *                       tiles (128 threads, three CTAs per SM, 64-sample chunks), and the
+ *                       pair mode, 1 x 1, in which every pair a wave needs is evaluated
+ *                       whole by one warp (no tile, so no pair slot is computed in vain;
+ *                       waves of up to 16 columns).  Records the fastest for the bucket of
+ *                       the batch's largest p and n, returns it in *tile_rows, *tile_cols,
+ *                       and ms[0..4] (if not NULL) receive the times with 64 x 32, 32 x 32,
+ *                       64 x 16, 32 x 16 and 1 x 1.  Costs fifteen batch calls; the
+ *                       workspace is as for lingam_fit_batch.  LINGAM_EINVAL for the FP64
+ *                       path.
  * lingam_autotune_reset -- forgets every measured choice (both tables).
  * The tables are shared by all threads of the process (guarded by a mutex).
  */
@@ -286,7 +290,8 @@ size_t lingam_workspace_size_batch(int count, const long long* p, const long lon
  * run without a graph.  opts->forced_order and opts->prior must be NULL, and
  * opts->max_iters and opts->gamma0 0; opts->split_n is ignored.  Pair tiles: on the
  * mixed path opts->tile_i x opts->tile_j for every problem of the call (64 x 32, 32 x 32,
- * 64 x 16 or 32 x 16), or, with both 0, the batch autotuner's shape for the largest p and n
+ * 64 x 16, 32 x 16, or 1 x 1: one pair per warp, which needs opts->reuse = 1 and otherwise
+ * runs 64 x 16), or, with both 0, the batch autotuner's shape for the largest p and n
  * (lingam_batch_tile_rows/_cols); 32 x 32 on the FP64 path.
  */
 int lingam_fit_batch(int count, const void* const* X, const long long* p, const long long* n, int* const* order,

@@ -2303,6 +2303,242 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
     }
 }
 
+// ------------------------------------------------------------------ batches: one pair per warp
+// The pair mode of the batch kernel, for many small problems: a wave's needed pairs (its
+// columns against each other and against the other rows, Sec. III-A) are enumerated and each
+// is evaluated whole by one warp (every sample of the pair, lane l taking the 32-sample
+// groups l, l + 32, ...), so no pair slot of a tile is computed in vain.
+// The per-sample arithmetic, the group closing and the pair measure are the tile path's; the
+// lanes' group sums are added in a tree.  Each problem's pair measures go to its I buffer; one CTA per
+// problem then sums its rows' and columns' contributions in a fixed order and runs the wave
+// finalisation.  Waves have up to kPairTJ columns; a wave has one nominal "tile" of kPairTI
+// rows (the finalisation's column parts: part 0 holds the sums, the others stay zero).
+constexpr int kPairTJ = 16;
+constexpr int kPairTI = 1024;
+constexpr int kPairThr = 256;
+constexpr int kPairLanes = 32;   // lanes per pair (8 per pair measured slower on long rows: n = 8000)
+
+// Unordered pair q of a wave with ncol columns and nrow rows (columns first): column c of
+// row slot e, for c < ncol <= e (the columns against the other rows), then c < e < ncol
+// (the columns' own triangle).
+__device__ __forceinline__ void pair_of(long long q, int ncol, int nrow, int& e, int& c) {
+    const long long cross = (long long)ncol * (nrow - ncol);
+    if (q < cross) {
+        e = ncol + int(q / ncol);
+        c = int(q % ncol);
+    } else {
+        const long long t = q - cross;   // triangle index: e (e - 1) / 2 + c, c < e
+        int ee = int((1.0 + sqrt(1.0 + 8.0 * double(t))) * 0.5);
+        while ((long long)ee * (ee - 1) / 2 > t) --ee;
+        while ((long long)(ee + 1) * ee / 2 <= t) ++ee;
+        e = ee;
+        c = int(t - (long long)ee * (ee - 1) / 2);
+    }
+}
+__device__ __forceinline__ long long wave_pairs(int ncol, int nrow) {
+    return (long long)ncol * (ncol - 1) / 2 + (long long)ncol * (nrow - ncol);
+}
+
+// One pair (row variable vi, column variable vj) by LPP consecutive lanes of a warp (the
+// warp takes 32 / LPP pairs at once, so their loads are in flight together); the measure I
+// to the first of them.  Lanes with no pair (have = false) only take part in the shuffles.
+template <int LPP>
+__device__ __forceinline__ float pair_by_lanes(const Fit& f, bool have, int vi, int vj, bool& degenerate) {
+    const int sl = (threadIdx.x & 31) % LPP;
+    float Da = 0.f, Ga = 0.f, Db = 0.f, Gb = 0.f;
+    float4 si = make_float4(0.f, 0.f, 0.f, 0.f), sj = si;
+    degenerate = false;
+    if (have) {
+        const int p = f.p, ld = f.ld;
+        float2 ro = __ldcg(f.sigf + size_t(vi) * p + vj);
+        degenerate = !(ro.y > float(degenerate_om(true)));
+        if (degenerate) ro = make_float2(0.f, 1.f);
+        const float sc = kScale / sqrtf(ro.y);
+        const float2 s2 = make_float2(sc, sc), sr2 = make_float2(-sc * ro.x, -sc * ro.x);
+        si = __ldcg(f.vstat + vi);
+        sj = __ldcg(f.vstat + vj);
+        const float* xi = static_cast<const float*>(f.xt) + size_t(vi) * ld;
+        const float* xj = static_cast<const float*>(f.xt) + size_t(vj) * ld;
+        for (int g = sl; g < ld / kSub; g += LPP) {
+            Acc2 aa, ab;
+            aa.A = ab.A = make_float2(0.f, 0.f);
+            aa.P = ab.P = make_float2(1.f, 1.f);
+            aa.G = ab.G = make_float2(0.f, 0.f);
+            const float4* ri = reinterpret_cast<const float4*>(xi + size_t(g) * kSub);
+            const float4* rj = reinterpret_cast<const float4*>(xj + size_t(g) * kSub);
+#pragma unroll 4
+            for (int k = 0; k < kSub / 4; ++k) {
+                const float4 a4 = ri[k], b4 = rj[k];
+                const float2 vi2[2] = {make_float2(a4.x, a4.y), make_float2(a4.z, a4.w)};
+                const float2 vj2[2] = {make_float2(b4.x, b4.y), make_float2(b4.z, b4.w)};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    acc2_add(aa, __ffma2_rn(s2, vi2[h], __fmul2_rn(sr2, vj2[h])));
+                    acc2_add(ab, __ffma2_rn(s2, vj2[h], __fmul2_rn(sr2, vi2[h])));
+                }
+            }
+            Da += fmaf(float(kLn2), lg2_approx(aa.P.x * aa.P.y), fmaf(aa.A.x + aa.A.y, kInvScale / -kC3, si.w));
+            Ga += aa.G.x + aa.G.y;
+            Db += fmaf(float(kLn2), lg2_approx(ab.P.x * ab.P.y), fmaf(ab.A.x + ab.A.y, kInvScale / -kC3, sj.w));
+            Gb += ab.G.x + ab.G.y;
+        }
+    }
+#pragma unroll
+    for (int o = LPP / 2; o > 0; o >>= 1) {
+        Da += __shfl_xor_sync(0xffffffffu, Da, o);
+        Ga += __shfl_xor_sync(0xffffffffu, Ga, o);
+        Db += __shfl_xor_sync(0xffffffffu, Db, o);
+        Gb += __shfl_xor_sync(0xffffffffu, Gb, o);
+    }
+    return have ? pair_measure_f(Da, Ga, Db, Gb, si, sj, __frcp_rn(float(f.n))) : 0.f;
+}
+
+// One problem's wave after its pairs: the rows' contributions sum_c min(0, I)^2 (a thread per
+// row) and the columns' sum_e max(0, I)^2 (a warp per column, lanes over the rows, then a
+// tree), float-float in a fixed order, into the buffers the finalisation reads.
+template <int NTH>
+__device__ void pairs_merge(const Fit& f, const Wave& wv) {
+    const int ncol = wv.ncol, nrow = wv.nrow, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const float* I = static_cast<const float*>(f.ibuf);
+    for (int e = tid; e < nrow; e += NTH) {
+        FF acc;
+        const int cmax = e < ncol ? e : ncol;   // the pairs of row slot e
+        for (int c = 0; c < cmax; ++c) acc.add_sq(fminf(I[size_t(e) * kPairTJ + c], 0.f));
+        f.rowsum[e] = acc.value();
+    }
+    constexpr int PARTS = NTH / 64;
+    const int nparts = wv.ntiles * PARTS;
+    for (int c = wid; c < kPairTJ; c += NTH / 32) {
+        FF acc;
+        if (c < ncol)
+            for (int e = c + 1 + lane; e < nrow; e += 32) acc.add_sq(fmaxf(I[size_t(e) * kPairTJ + c], 0.f));
+        float2 v = make_float2(acc.hi, acc.lo);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float2 w = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+            v = ff_add(v, w);
+        }
+        for (int at = lane; at < nparts; at += 32) {
+            const float2 ff = at == 0 ? v : make_float2(0.f, 0.f);
+            f.colsum[size_t(at) * kPairTJ + c] = *reinterpret_cast<const double*>(&ff);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPairThr, 2) k_batch_pairs(const Fit* __restrict__ fits, int count, int maxp,
+                                                             Ctl* bctl) {
+    unsigned char* smem_raw = smem_dyn;
+    __shared__ IterShared sh;
+    __shared__ BatchShared bs;
+    constexpr int NW = kPairThr / 32;
+    volatile Ctl* vb = bctl;
+    if (vb->status != 0) return;
+    const unsigned long long tmo = vb->timeout_ns;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int it = 0; it < maxp; ++it) {
+        batch_active(fits, count, it, 0, bs);
+        for (int d = blockIdx.x; d < count; d += gridDim.x)
+            if (bs.act[d]) plan_phase<kPairThr, kPairTI, kPairTJ, 2048>(fits[d], it, smem_raw, sh.red, fits[d].sigma);
+        if (!grid_sync(bctl, tmo)) return;
+        for (;;) {
+            // the wave of every problem whose iteration is not done, and its pairs' offsets
+            // (a wave may have no pair left to evaluate, one column whose partners were all
+            // columns before: it is still finalised)
+            long long pbase = 0, nact = 0;
+            for (int base = 0; base < count; base += kPairThr) {
+                const int d = base + int(threadIdx.x);
+                long long q = 0, a = 0;
+                if (d < count) {
+                    const Fit& f = fits[d];
+                    volatile Ctl* c = f.ctl;
+                    Wave w = {0, 0, 0};
+                    if (it < f.p && !c->done && c->status == 0) {
+                        w = {c->ntiles, c->ncol, c->nrow};
+                        q = wave_pairs(w.ncol, w.nrow);
+                        a = 1;
+                    }
+                    bs.wave[d] = w;
+                    bs.act[d] = (unsigned char)a;
+                }
+                long long tq, ta;
+                const long long eq = block_excl_scan<kPairThr>(q, sh.lred, &tq);
+                block_excl_scan<kPairThr>(a, sh.lred, &ta);
+                if (d < count) bs.uoff[d] = pbase + eq;
+                pbase += tq;
+                nact += ta;
+            }
+            if (threadIdx.x == 0) bs.uoff[count] = pbase;
+            __syncthreads();
+            const long long ptot = bs.uoff[count];
+            if (nact == 0) break;
+            // every needed pair of every problem, kPairLanes lanes per pair (a warp takes
+            // 32 / kPairLanes pairs at a time)
+            constexpr int PPW = 32 / kPairLanes;
+            const int sub = lane / kPairLanes;
+            for (long long base = ((long long)blockIdx.x * NW + wid) * PPW; base < ptot;
+                 base += (long long)gridDim.x * NW * PPW) {
+                const long long g = base + sub;
+                const bool have = g < ptot;
+                const int d = have ? last_le(bs.uoff, count, g) : 0;
+                const Fit& f = fits[d];
+                int e = 0, c = 0, vi = 0, vj = 0;
+                if (have) {
+                    const Wave wv = bs.wave[d];
+                    pair_of(g - bs.uoff[d], wv.ncol, wv.nrow, e, c);
+                    vi = ld2(f.rows + e);
+                    vj = ld2(f.cols + c);
+                }
+                bool degenerate;
+                const float I = pair_by_lanes<kPairLanes>(f, have, vi, vj, degenerate);
+                if (have && lane % kPairLanes == 0) {
+                    if (degenerate || !isfinite(I)) set_status(f.ctl, LINGAM_EDEGENERATE);
+                    static_cast<float*>(f.ibuf)[size_t(e) * kPairTJ + c] = I;
+                }
+            }
+            if (!grid_sync(bctl, tmo)) return;
+            // each problem's sums and finalisation, one CTA per problem
+            for (int d = blockIdx.x; d < count; d += gridDim.x) {
+                if (!bs.act[d]) continue;
+                pairs_merge<kPairThr>(fits[d], bs.wave[d]);
+                __syncthreads();   // the sums precede the finalisation's reads (same CTA)
+                wave_finalize<kPairThr, kPairTI, kPairTJ>(fits[d], bs.wave[d], it, sh.red, 0u);
+                __syncthreads();
+            }
+            if (!grid_sync(bctl, tmo)) return;
+        }
+        // UpdateData and UpdateCovMat of every problem that took a root (the tile path's)
+        batch_active(fits, count, it, 1, bs);
+        int rtot;
+        long long etot;
+        batch_removal_layout<kPairThr>(fits, count, bs, sh, rtot, etot);
+        batch_remove_data<CfgF16>(fits, count, bs, rtot);
+        batch_remove_cov<CfgF16>(fits, count, bs, etot);
+        if (!grid_sync(bctl, tmo)) return;
+    }
+}
+
+static cudaError_t launch_batch_pairs(const Fit* fits_dev, int count, int maxp, Ctl* bctl, int nsm, cudaStream_t st) {
+    const size_t smem = size_t(2048) * sizeof(unsigned long long);   // the candidate sort
+    cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(k_batch_pairs), smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pairs, kPairThr, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    cudaLaunchConfig_t cfg = {};
+    const int grid = nsm * (per_sm < 2 ? per_sm : 2);
+    cfg.gridDim = dim3(grid < kMaxGrid ? grid : kMaxGrid);
+    cfg.blockDim = dim3(kPairThr);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch_pairs, fits_dev, count, maxp, bctl);
+}
+
 // ------------------------------------------------------------------ host side
 template <class Cfg>
 static int grid_for(int nsm) {
@@ -2370,6 +2606,7 @@ cudaError_t launch_batch(const Fit* fits_dev, int count, int maxp, int precision
     if (tile_rows == 64 && tile_cols == 16) return launch_batch_cfg<CfgF16>(fits_dev, count, maxp, bctl, nsm, st);
     if (tile_rows == 32 && tile_cols == 32) return launch_batch_cfg<CfgF32>(fits_dev, count, maxp, bctl, nsm, st);
     if (tile_rows == 32 && tile_cols == 16) return launch_batch_cfg<CfgB>(fits_dev, count, maxp, bctl, nsm, st);
+    if (tile_rows == 1 && tile_cols == 1) return launch_batch_pairs(fits_dev, count, maxp, bctl, nsm, st);
     return cudaErrorInvalidValue;
 }
 

@@ -147,8 +147,9 @@ static TileShape choose_tile(long long p, long long n, int tile_i, int tile_j) {
 static bool valid_opts(const lingam_opts& o) {
     return (o.precision == LINGAM_MIXED || o.precision == LINGAM_FP64) &&
            (o.input_dtype == LINGAM_F32 || o.input_dtype == LINGAM_F64) && (o.prune == 0 || o.prune == 1) &&
-           (o.reuse == 0 || o.reuse == 1) && o.split_n >= 0 && (o.tile_i == 0 || o.tile_i == 32 || o.tile_i == 64) &&
-           (o.tile_j == 0 || o.tile_j == 16 || o.tile_j == 32) &&
+           (o.reuse == 0 || o.reuse == 1) && o.split_n >= 0 &&
+           ((o.tile_i == 1 && o.tile_j == 1) ||   // the batch kernel's pair-per-warp mode
+            ((o.tile_i == 0 || o.tile_i == 32 || o.tile_i == 64) && (o.tile_j == 0 || o.tile_j == 16 || o.tile_j == 32))) &&
            std::isfinite(o.gamma0) && o.gamma0 >= 0.0 &&
            (o.gamma0 == 0.0 || (o.prune == 1 && o.reuse == 1 && std::isfinite(o.gamma_c) && o.gamma_c > 1.0));
 }
@@ -157,12 +158,16 @@ static bool valid_opts(const lingam_opts& o) {
 // autotuner's table for the largest p and n; the FP64 path has 32 x 32 tiles only.
 static TileShape batch_tile_shape(const lingam_opts& o, long long maxp, long long maxn) {
     if (o.precision != LINGAM_MIXED) return TileShape{32, 32};
+    if (o.tile_i == 1 && o.tile_j == 1 && !o.reuse) return TileShape{64, 16};   // pair mode evaluates unordered pairs
     if (o.tile_i != 0 || o.tile_j != 0) return TileShape{o.tile_i ? o.tile_i : 64, o.tile_j ? o.tile_j : 32};
     return autotune_batch_shape(maxp, maxn);
 }
 
-// Single fits run 64 x 32, 32 x 32 or 64 x 16 tiles (32 x 16 tiles are a batch shape).
-static bool single_fit_shape(const lingam_opts& o) { return !(o.tile_i == 32 && o.tile_j == 16); }
+// Single fits run 64 x 32, 32 x 32 or 64 x 16 tiles (32 x 16 tiles and the pair-per-warp
+// mode, 1 x 1, are batch shapes).
+static bool single_fit_shape(const lingam_opts& o) {
+    return !(o.tile_i == 32 && o.tile_j == 16) && !(o.tile_i == 1 && o.tile_j == 1);
+}
 
 static bool is_device_ptr(const void* ptr) {
     cudaPointerAttributes a;
@@ -1054,10 +1059,10 @@ int lingam_autotune_batch(int count, const void* const* X, const long long* p, c
         ord[size_t(k)].resize(size_t(p[k]));
         op[size_t(k)] = ord[size_t(k)].data();
     }
-    const TileShape cand[4] = {{64, 32}, {32, 32}, {64, 16}, {32, 16}};
-    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    const TileShape cand[5] = {{64, 32}, {32, 32}, {64, 16}, {32, 16}, {1, 1}};
+    double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     int best = 0;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 5; ++c) {
         lingam_opts oc = o;
         oc.tile_i = cand[c].rows;
         oc.tile_j = cand[c].cols;
@@ -1076,7 +1081,7 @@ int lingam_autotune_batch(int count, const void* const* X, const long long* p, c
     *tile_rows = cand[best].rows;
     *tile_cols = cand[best].cols;
     if (ms)
-        for (int c = 0; c < 4; ++c) ms[c] = t[c];
+        for (int c = 0; c < 5; ++c) ms[c] = t[c];
     return LINGAM_OK;
 }
 

@@ -333,7 +333,8 @@ def autotune(X, stream=None, workspace=None):
 
 def autotune_batch(Xs, stream=None, workspace=None):
     """lingam_autotune_batch on a list of datasets: times lingam_fit_batch with 64x32, 32x32,
-    64x16 and 32x16 pair tiles, records the fastest for the bucket of the largest p and n;
+    64x16 and 32x16 pair tiles and the pair-per-warp mode (1x1), records the fastest for the
+    bucket of the largest p and n;
     returns ((rows, cols), {shape: ms})."""
     L = load()
     torch = _torch()
@@ -349,14 +350,14 @@ def autotune_batch(Xs, stream=None, workspace=None):
         workspace = alloc_workspace(need)
     xp = (ctypes.c_void_p * count)(*[it[0] for it in items])
     tr, tc = ctypes.c_int(0), ctypes.c_int(0)
-    ms = (ctypes.c_double * 4)()
+    ms = (ctypes.c_double * 5)()
     st = L.lingam_autotune_batch(count, xp, pa, na, ctypes.c_void_p(workspace.data_ptr()), ctypes.byref(o),
                                  ctypes.byref(tr), ctypes.byref(tc), ms)
     del items
     if st != LINGAM_OK:
         raise LingamError(st, status_string(st))
     return (int(tr.value), int(tc.value)), {(64, 32): float(ms[0]), (32, 32): float(ms[1]), (64, 16): float(ms[2]),
-                                            (32, 16): float(ms[3])}
+                                            (32, 16): float(ms[3]), (1, 1): float(ms[4])}
 
 
 def batch_tile_shape(maxp: int, maxn: int) -> tuple[int, int]:

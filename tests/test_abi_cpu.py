@@ -87,6 +87,11 @@ def test_tile_rows_default_rule(lib):
     ns = (ctypes.c_longlong * 1)(100)
     assert lib.lingam_workspace_size_batch(1, ps, ns, ctypes.byref(o)) > 0
     assert lib.lingam_workspace_size(10, 100, ctypes.byref(o)) == 0
+    o.tile_i, o.tile_j = 1, 1   # the batch pair-per-warp mode
+    assert lib.lingam_workspace_size_batch(1, ps, ns, ctypes.byref(o)) > 0
+    assert lib.lingam_workspace_size(10, 100, ctypes.byref(o)) == 0
+    o.tile_i, o.tile_j = 1, 32
+    assert lib.lingam_workspace_size_batch(1, ps, ns, ctypes.byref(o)) == 0
 
 
 def test_batch_and_bootstrap_workspace_sizes(lib):

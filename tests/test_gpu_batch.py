@@ -130,7 +130,7 @@ def _hard_members(rng_seed):
     return [Xh.astype(np.float32), Xc.astype(np.float32)]
 
 
-@pytest.mark.parametrize("tile_i,tile_j", [(0, 0), (64, 32), (64, 16), (32, 16)])
+@pytest.mark.parametrize("tile_i,tile_j", [(0, 0), (64, 32), (64, 16), (32, 16), (1, 1)])
 def test_batch_matches_oracle(tile_i, tile_j):
     """Batch members (uneven sizes, one above 64 variables, plus a heavy-tailed and a
     near-collinear member) against the oracle, with each pair-tile shape of the batch kernel
