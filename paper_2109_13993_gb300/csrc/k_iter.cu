@@ -2306,8 +2306,7 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
 // ------------------------------------------------------------------ batches: one pair per warp
 // The pair mode of the batch kernel, for many small problems: a wave's needed pairs (its
 // columns against each other and against the other rows, Sec. III-A) are enumerated and each
-// is evaluated whole by one warp (every sample of the pair, lane l taking the 32-sample
-// groups l, l + 32, ...), so no pair slot of a tile is computed in vain.
+// is evaluated whole by one warp, so no pair slot of a tile is computed in vain.
 // The per-sample arithmetic, the group closing and the pair measure are the tile path's; the
 // lanes' group sums are added in a tree.  Each problem's pair measures go to its I buffer; one CTA per
 // problem then sums its rows' and columns' contributions in a fixed order and runs the wave
@@ -2316,81 +2315,107 @@ __global__ void __launch_bounds__(Cfg::CONS, Cfg::MINB) k_batch(const Fit* __res
 constexpr int kPairTJ = 16;
 constexpr int kPairTI = 1024;
 constexpr int kPairThr = 256;
-constexpr int kPairLanes = 32;   // lanes per pair (8 per pair measured slower on long rows: n = 8000)
 
 // Unordered pair q of a wave with ncol columns and nrow rows (columns first): column c of
 // row slot e, for c < ncol <= e (the columns against the other rows), then c < e < ncol
 // (the columns' own triangle).
 __device__ __forceinline__ void pair_of(long long q, int ncol, int nrow, int& e, int& c) {
-    const long long cross = (long long)ncol * (nrow - ncol);
-    if (q < cross) {
-        e = ncol + int(q / ncol);
-        c = int(q % ncol);
+    const int qq = int(q);   // below ncol * nrow <= kPairTJ * 16384
+    const int cross = ncol * (nrow - ncol);
+    if (qq < cross) {
+        const int k = qq / ncol;
+        e = ncol + k;
+        c = qq - k * ncol;
     } else {
-        const long long t = q - cross;   // triangle index: e (e - 1) / 2 + c, c < e
-        int ee = int((1.0 + sqrt(1.0 + 8.0 * double(t))) * 0.5);
-        while ((long long)ee * (ee - 1) / 2 > t) --ee;
-        while ((long long)(ee + 1) * ee / 2 <= t) ++ee;
+        const int t = qq - cross;   // triangle index: e (e - 1) / 2 + c, c < e < ncol <= kPairTJ
+        int ee = 1;
+        while ((ee + 1) * ee / 2 <= t) ++ee;
         e = ee;
-        c = int(t - (long long)ee * (ee - 1) / 2);
+        c = t - ee * (ee - 1) / 2;
     }
 }
 __device__ __forceinline__ long long wave_pairs(int ncol, int nrow) {
     return (long long)ncol * (ncol - 1) / 2 + (long long)ncol * (nrow - ncol);
 }
 
-// One pair (row variable vi, column variable vj) by LPP consecutive lanes of a warp (the
-// warp takes 32 / LPP pairs at once, so their loads are in flight together); the measure I
-// to the first of them.  Lanes with no pair (have = false) only take part in the shuffles.
-template <int LPP>
-__device__ __forceinline__ float pair_by_lanes(const Fit& f, bool have, int vi, int vj, bool& degenerate) {
-    const int sl = (threadIdx.x & 31) % LPP;
-    float Da = 0.f, Ga = 0.f, Db = 0.f, Gb = 0.f;
-    float4 si = make_float4(0.f, 0.f, 0.f, 0.f), sj = si;
-    degenerate = false;
-    if (have) {
-        const int p = f.p, ld = f.ld;
-        float2 ro = __ldcg(f.sigf + size_t(vi) * p + vj);
-        degenerate = !(ro.y > float(degenerate_om(true)));
-        if (degenerate) ro = make_float2(0.f, 1.f);
-        const float sc = kScale / sqrtf(ro.y);
-        const float2 s2 = make_float2(sc, sc), sr2 = make_float2(-sc * ro.x, -sc * ro.x);
-        si = __ldcg(f.vstat + vi);
-        sj = __ldcg(f.vstat + vj);
-        const float* xi = static_cast<const float*>(f.xt) + size_t(vi) * ld;
-        const float* xj = static_cast<const float*>(f.xt) + size_t(vj) * ld;
-        for (int g = sl; g < ld / kSub; g += LPP) {
-            Acc2 aa, ab;
-            aa.A = ab.A = make_float2(0.f, 0.f);
-            aa.P = ab.P = make_float2(1.f, 1.f);
-            aa.G = ab.G = make_float2(0.f, 0.f);
-            const float4* ri = reinterpret_cast<const float4*>(xi + size_t(g) * kSub);
-            const float4* rj = reinterpret_cast<const float4*>(xj + size_t(g) * kSub);
-#pragma unroll 4
-            for (int k = 0; k < kSub / 4; ++k) {
-                const float4 a4 = ri[k], b4 = rj[k];
-                const float2 vi2[2] = {make_float2(a4.x, a4.y), make_float2(a4.z, a4.w)};
-                const float2 vj2[2] = {make_float2(b4.x, b4.y), make_float2(b4.z, b4.w)};
+// Closes one 32-sample group of both directions into the lane's sums (the tile path's group
+// closing: one lg2 of the product, the centring offset .w of each variable).
+__device__ __forceinline__ void close_group(const Acc2& aa, const Acc2& ab, float4 si, float4 sj, float& Da,
+                                            float& Ga, float& Db, float& Gb) {
+    Da += fmaf(float(kLn2), lg2_approx(aa.P.x * aa.P.y), fmaf(aa.A.x + aa.A.y, kInvScale / -kC3, si.w));
+    Ga += aa.G.x + aa.G.y;
+    Db += fmaf(float(kLn2), lg2_approx(ab.P.x * ab.P.y), fmaf(ab.A.x + ab.A.y, kInvScale / -kC3, sj.w));
+    Gb += ab.G.x + ab.G.y;
+}
+__device__ __forceinline__ void acc_pair4(Acc2& aa, Acc2& ab, float4 a4, float4 b4, float2 s2, float2 sr2) {
+    const float2 vi2[2] = {make_float2(a4.x, a4.y), make_float2(a4.z, a4.w)};
+    const float2 vj2[2] = {make_float2(b4.x, b4.y), make_float2(b4.z, b4.w)};
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    acc2_add(aa, __ffma2_rn(s2, vi2[h], __fmul2_rn(sr2, vj2[h])));
-                    acc2_add(ab, __ffma2_rn(s2, vj2[h], __fmul2_rn(sr2, vi2[h])));
-                }
-            }
-            Da += fmaf(float(kLn2), lg2_approx(aa.P.x * aa.P.y), fmaf(aa.A.x + aa.A.y, kInvScale / -kC3, si.w));
-            Ga += aa.G.x + aa.G.y;
-            Db += fmaf(float(kLn2), lg2_approx(ab.P.x * ab.P.y), fmaf(ab.A.x + ab.A.y, kInvScale / -kC3, sj.w));
-            Gb += ab.G.x + ab.G.y;
+    for (int h = 0; h < 2; ++h) {
+        acc2_add(aa, __ffma2_rn(s2, vi2[h], __fmul2_rn(sr2, vj2[h])));
+        acc2_add(ab, __ffma2_rn(s2, vj2[h], __fmul2_rn(sr2, vi2[h])));
+    }
+}
+__device__ __forceinline__ void acc_init(Acc2& a) {
+    a.A = make_float2(0.f, 0.f);
+    a.P = make_float2(1.f, 1.f);
+    a.G = make_float2(0.f, 0.f);
+}
+
+// One pair (row variable vi, column variable vj) by a whole warp; the measure I to every lane.
+// A 32-sample group of a lane is any 32 of the row's samples (the centring offset is per group
+// and the padding samples are zero), so the reads are coalesced: in each block of 1024
+// samples lane l takes the four samples 4l .. 4l + 3 of each 128-sample chunk, eight chunks
+// making its group.  The rows' last ld mod 1024 samples (a multiple of 128) are closed as
+// whole 32-sample groups, one per lane.
+__device__ __forceinline__ float pair_by_warp(const Fit& f, int vi, int vj, bool& degenerate) {
+    const int lane = threadIdx.x & 31;
+    const int p = f.p, ld = f.ld;
+    float2 ro = __ldcg(f.sigf + size_t(vi) * p + vj);
+    degenerate = !(ro.y > float(degenerate_om(true)));
+    if (degenerate) ro = make_float2(0.f, 1.f);
+    const float sc = kScale / sqrtf(ro.y);
+    const float2 s2 = make_float2(sc, sc), sr2 = make_float2(-sc * ro.x, -sc * ro.x);
+    const float4 si = __ldcg(f.vstat + vi), sj = __ldcg(f.vstat + vj);
+    const float* xi = static_cast<const float*>(f.xt) + size_t(vi) * ld;
+    const float* xj = static_cast<const float*>(f.xt) + size_t(vj) * ld;
+    float Da = 0.f, Ga = 0.f, Db = 0.f, Gb = 0.f;
+    const int nblk = ld >> 10;
+    for (int b = 0; b < nblk; ++b) {
+        const float4* ri = reinterpret_cast<const float4*>(xi + (size_t(b) << 10)) + lane;
+        const float4* rj = reinterpret_cast<const float4*>(xj + (size_t(b) << 10)) + lane;
+        float4 a4[8], b4[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            a4[k] = ri[32 * k];
+            b4[k] = rj[32 * k];
         }
+        Acc2 aa, ab;
+        acc_init(aa);
+        acc_init(ab);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc_pair4(aa, ab, a4[k], b4[k], s2, sr2);
+        close_group(aa, ab, si, sj, Da, Ga, Db, Gb);
+    }
+    const int g = (nblk << 5) + lane;   // tail: one contiguous group per lane
+    if (g < ld / kSub) {
+        const float4* ri = reinterpret_cast<const float4*>(xi + size_t(g) * kSub);
+        const float4* rj = reinterpret_cast<const float4*>(xj + size_t(g) * kSub);
+        Acc2 aa, ab;
+        acc_init(aa);
+        acc_init(ab);
+#pragma unroll 4
+        for (int k = 0; k < kSub / 4; ++k) acc_pair4(aa, ab, ri[k], rj[k], s2, sr2);
+        close_group(aa, ab, si, sj, Da, Ga, Db, Gb);
     }
 #pragma unroll
-    for (int o = LPP / 2; o > 0; o >>= 1) {
+    for (int o = 16; o > 0; o >>= 1) {
         Da += __shfl_xor_sync(0xffffffffu, Da, o);
         Ga += __shfl_xor_sync(0xffffffffu, Ga, o);
         Db += __shfl_xor_sync(0xffffffffu, Db, o);
         Gb += __shfl_xor_sync(0xffffffffu, Gb, o);
     }
-    return have ? pair_measure_f(Da, Ga, Db, Gb, si, sj, __frcp_rn(float(f.n))) : 0.f;
+    return pair_measure_f(Da, Ga, Db, Gb, si, sj, __frcp_rn(float(f.n)));
 }
 
 // One problem's wave after its pairs: the rows' contributions sum_c min(0, I)^2 (a thread per
@@ -2471,26 +2496,16 @@ __global__ void __launch_bounds__(kPairThr, 2) k_batch_pairs(const Fit* __restri
             __syncthreads();
             const long long ptot = bs.uoff[count];
             if (nact == 0) break;
-            // every needed pair of every problem, kPairLanes lanes per pair (a warp takes
-            // 32 / kPairLanes pairs at a time)
-            constexpr int PPW = 32 / kPairLanes;
-            const int sub = lane / kPairLanes;
-            for (long long base = ((long long)blockIdx.x * NW + wid) * PPW; base < ptot;
-                 base += (long long)gridDim.x * NW * PPW) {
-                const long long g = base + sub;
-                const bool have = g < ptot;
-                const int d = have ? last_le(bs.uoff, count, g) : 0;
+            // every needed pair of every problem, one warp per pair
+            for (long long g = (long long)blockIdx.x * NW + wid; g < ptot; g += (long long)gridDim.x * NW) {
+                const int d = last_le(bs.uoff, count, g);
                 const Fit& f = fits[d];
-                int e = 0, c = 0, vi = 0, vj = 0;
-                if (have) {
-                    const Wave wv = bs.wave[d];
-                    pair_of(g - bs.uoff[d], wv.ncol, wv.nrow, e, c);
-                    vi = ld2(f.rows + e);
-                    vj = ld2(f.cols + c);
-                }
+                const Wave wv = bs.wave[d];
+                int e, c;
+                pair_of(g - bs.uoff[d], wv.ncol, wv.nrow, e, c);
                 bool degenerate;
-                const float I = pair_by_lanes<kPairLanes>(f, have, vi, vj, degenerate);
-                if (have && lane % kPairLanes == 0) {
+                const float I = pair_by_warp(f, ld2(f.rows + e), ld2(f.cols + c), degenerate);
+                if (lane == 0) {
                     if (degenerate || !isfinite(I)) set_status(f.ctl, LINGAM_EDEGENERATE);
                     static_cast<float*>(f.ibuf)[size_t(e) * kPairTJ + c] = I;
                 }
