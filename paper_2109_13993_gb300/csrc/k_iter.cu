@@ -2137,9 +2137,10 @@ __device__ void batch_removal_layout(const Fit* fits, int count, BatchShared& bs
     etot = ebase;
 }
 
-// UpdateData (Algorithm 7) with the new H(x_w), one warp per row of any problem: lanes
-// take float4 (FP32 path) or single samples, sum the moments in the working precision in
-// blocks of 8 steps, flushed into FP64, and the warp tree is FP64.
+// UpdateData (Algorithm 7) with the new H(x_w), one warp per row of any problem.  On the
+// FP32 path lanes take float4, sum the moments of 32 samples in FP32 and flush them into
+// float-float sums, and the warp tree is float-float (FP64 adds are slow on this part).  The
+// FP64 path sums single samples in FP64.
 template <class Cfg>
 __device__ __noinline__ void batch_remove_data(const Fit* fits, int count, const BatchShared& bs, int rtot) {
     using T = typename Cfg::T;
@@ -2161,6 +2162,7 @@ __device__ __noinline__ void batch_remove_data(const Fit* fits, int count, const
             float4* xw4 = reinterpret_cast<float4*>(xw);
             const float4* xr4 = reinterpret_cast<const float4*>(xr);
             const int n4 = ld / 4;
+            float2 Lf = make_float2(0.f, 0.f), Gf = make_float2(0.f, 0.f);
             for (int b0 = lane; b0 < n4; b0 += 32 * 8) {
                 float lcc = 0.f, g = 0.f;
 #pragma unroll
@@ -2181,24 +2183,31 @@ __device__ __noinline__ void batch_remove_data(const Fit* fits, int count, const
                         if (t + 3 < n) mom_add(o.w, lcc, g);
                     }
                 }
-                L += double(lcc);
-                Gs += double(g);
+                Lf = ff_add(Lf, make_float2(lcc, 0.f));
+                Gf = ff_add(Gf, make_float2(g, 0.f));
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                Lf = ff_add(Lf, make_float2(__shfl_xor_sync(0xffffffffu, Lf.x, o), __shfl_xor_sync(0xffffffffu, Lf.y, o)));
+                Gf = ff_add(Gf, make_float2(__shfl_xor_sync(0xffffffffu, Gf.x, o), __shfl_xor_sync(0xffffffffu, Gf.y, o)));
+            }
+            L = double(Lf.x) + double(Lf.y);
+            Gs = double(Gf.x) + double(Gf.y);
         } else {
             for (int t = lane; t < ld; t += 32) {
                 const double u = fma(-c, xr[t], xw[t]) * inv;
                 xw[t] = u;
                 if (t < n) mom_add(u, L, Gs);
             }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            L += __shfl_xor_sync(0xffffffffu, L, o);
-            Gs += __shfl_xor_sync(0xffffffffu, Gs, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                L += __shfl_xor_sync(0xffffffffu, L, o);
+                Gs += __shfl_xor_sync(0xffffffffu, Gs, o);
+            }
         }
         if (lane == 0) {
-            f.hx[w] = hterm(L, Gs, double(n));
-            f.vstat[w] = var_stats(L, Gs, n, ld);
+            f.hx[w] = hterm_inv(L, Gs, f.inv_n);
+            f.vstat[w] = var_stats_inv(L, Gs, n, ld, f.inv_n);
         }
     }
 }
@@ -2450,6 +2459,28 @@ __device__ void pairs_merge(const Fit& f, const Wave& wv) {
     }
 }
 
+// Every needed pair of every problem's wave, one warp per pair, into the problems' I
+// buffers.  Out of line, so that the sample loop's registers are allocated apart from the
+// rest of the kernel.
+__device__ __noinline__ void pairs_compute(const Fit* __restrict__ fits, int count, const BatchShared& bs,
+                                           long long ptot) {
+    constexpr int NW = kPairThr / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (long long g = (long long)blockIdx.x * NW + wid; g < ptot; g += (long long)gridDim.x * NW) {
+        const int d = last_le(bs.uoff, count, g);
+        const Fit& f = fits[d];
+        const Wave wv = bs.wave[d];
+        int e, c;
+        pair_of(g - bs.uoff[d], wv.ncol, wv.nrow, e, c);
+        bool degenerate;
+        const float I = pair_by_warp(f, ld2(f.rows + e), ld2(f.cols + c), degenerate);
+        if (lane == 0) {
+            if (degenerate || !isfinite(I)) set_status(f.ctl, LINGAM_EDEGENERATE);
+            static_cast<float*>(f.ibuf)[size_t(e) * kPairTJ + c] = I;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kPairThr, 2) k_batch_pairs(const Fit* __restrict__ fits, int count, int maxp,
                                                              Ctl* bctl) {
     unsigned char* smem_raw = smem_dyn;
@@ -2496,20 +2527,7 @@ __global__ void __launch_bounds__(kPairThr, 2) k_batch_pairs(const Fit* __restri
             __syncthreads();
             const long long ptot = bs.uoff[count];
             if (nact == 0) break;
-            // every needed pair of every problem, one warp per pair
-            for (long long g = (long long)blockIdx.x * NW + wid; g < ptot; g += (long long)gridDim.x * NW) {
-                const int d = last_le(bs.uoff, count, g);
-                const Fit& f = fits[d];
-                const Wave wv = bs.wave[d];
-                int e, c;
-                pair_of(g - bs.uoff[d], wv.ncol, wv.nrow, e, c);
-                bool degenerate;
-                const float I = pair_by_warp(f, ld2(f.rows + e), ld2(f.cols + c), degenerate);
-                if (lane == 0) {
-                    if (degenerate || !isfinite(I)) set_status(f.ctl, LINGAM_EDEGENERATE);
-                    static_cast<float*>(f.ibuf)[size_t(e) * kPairTJ + c] = I;
-                }
-            }
+            pairs_compute(fits, count, bs, ptot);   // every needed pair of every problem
             if (!grid_sync(bctl, tmo)) return;
             // each problem's sums and finalisation, one CTA per problem
             for (int d = blockIdx.x; d < count; d += gridDim.x) {
