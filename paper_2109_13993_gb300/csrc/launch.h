@@ -25,6 +25,14 @@ cudaError_t launch_gram(const Fit& f, cudaStream_t st);
 // over 128 x 128 tiles of the upper triangle with the sample axis split over CTAs,
 // float-float partial tiles in `partial`, summed in FP64 into sig and sig0.
 cudaError_t launch_gram_tc(const Fit& f, void* digits, void* partial, cudaStream_t st);
+// The mixed path's Gram of every problem with p <= kSmallGramP and row length ld <=
+// kSmallGramLd of a batch table of up to kBatchLaunchMax problems, in one launch of `units`
+// CTAs (gram_small_batch_units of the table's p and ld); exact FP32 products summed in
+// float-float.  The other problems are skipped.
+constexpr int kSmallGramP = 128;
+constexpr int kSmallGramLd = 2048;
+int gram_small_batch_units(const long long* p, const int* ld, int count);
+cudaError_t launch_gram_small_batch(const Fit* fits_dev, int count, int units, cudaStream_t st);
 // Bytes of `digits` and of `partial` that launch_gram_tc needs for p variables and row length ld.
 size_t gram_tc_digit_bytes(long long p, int ld);
 size_t gram_tc_partial_bytes(long long p, int ld);

@@ -680,8 +680,25 @@ static cudaError_t enqueue_batch(char* ws, const BatchLayout& BL, const std::vec
             if (cudaStreamWaitEvent(fs->s[nfork], fs->fork, 0) != cudaSuccess) break;
     }
     cudaGetLastError();
-    for (int k = 0; k < count && e == cudaSuccess; ++k) {
-        cudaStream_t sk = nfork > 0 ? fs->s[k % nfork] : st;
+    // mixed path: the small problems (p <= kSmallGramP, ld <= kSmallGramLd) in one launch per
+    // table chunk on the caller's stream, the others one by one on the fork streams
+    const bool small_gram = o.precision == LINGAM_MIXED;
+    if (small_gram) {
+        std::vector<long long> ph(static_cast<size_t>(count));
+        std::vector<int> lh(static_cast<size_t>(count));
+        for (int k = 0; k < count; ++k) {
+            ph[size_t(k)] = fits[size_t(k)].p;
+            lh[size_t(k)] = fits[size_t(k)].ld;
+        }
+        for (int c0 = 0; c0 < count && e == cudaSuccess; c0 += kBatchLaunchMax) {
+            const int cnt = std::min(kBatchLaunchMax, count - c0);
+            const int units = gram_small_batch_units(ph.data() + c0, lh.data() + c0, cnt);
+            if (units > 0) e = launch_gram_small_batch(fits_dev + c0, cnt, units, st);
+        }
+    }
+    for (int k = 0, j = 0; k < count && e == cudaSuccess; ++k) {
+        if (small_gram && fits[size_t(k)].p <= kSmallGramP && fits[size_t(k)].ld <= kSmallGramLd) continue;
+        cudaStream_t sk = nfork > 0 ? fs->s[j++ % nfork] : st;
         e = o.precision == LINGAM_MIXED
                 ? launch_gram_tc(fits[size_t(k)], ws + BL.region[size_t(k)] + Ls[size_t(k)].off_xin, fits[size_t(k)].partials, sk)
                 : launch_gram(fits[size_t(k)], sk);

@@ -221,6 +221,25 @@ def test_batch_edge_sizes():
             assert np.abs(B - single.B).max() <= 1e-6 * max(1.0, np.abs(single.B).max())
 
 
+def test_batch_gram_small_and_large_members():
+    """Members on both sides of the batched small-problem covariance (p <= 128 in one launch,
+    exact FP32 products in float-float sums; larger p on the tensor-core Gram): every member
+    agrees with its single fit (tensor-core Gram) on the resolved prefix, and B within 1e-6
+    where the whole order agrees."""
+    sizes = [(3, 900), (50, 2000), (127, 1200), (128, 1100), (129, 1000), (140, 700)]
+    ds = [synth.lingam_dataset(p, n, min(1.0, 4.0 / (p - 1)), seed=120 + k).X.astype(np.float32)
+          for k, (p, n) in enumerate(sizes)]
+    Xs = [_dev(X) for X in ds]
+    res = lingam.fit_batch(Xs, precision="mixed", tile_i=1, tile_j=1)
+    assert res.status == 0 and np.all(res.statuses == 0)
+    for X, (p, n), o, B in zip(Xs, sizes, res.orders, res.Bs):
+        single, roots, margins = _single(X)
+        k = _agree_until_unresolved(o, single.order, roots, margins)
+        print(f"p={p} n={n}: batch order equals the single fit on {k} of {p} iterations")
+        if k == p:
+            assert np.abs(B - single.B).max() <= 1e-6 * max(1.0, np.abs(single.B).max())
+
+
 def test_batch_degenerate_member_does_not_stop_the_others():
     ds = [synth.lingam_dataset(10, 800, 0.3, seed=70 + k).X.astype(np.float32) for k in range(3)]
     ds[1][4] = 2.5   # a constant row
