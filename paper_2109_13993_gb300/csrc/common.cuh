@@ -229,6 +229,15 @@ __device__ __forceinline__ float lg2_approx(float x) {
     return y;
 }
 
+// Sum of two float-float values (hi, lo): TwoSum of the high parts, the low parts added to
+// its error, renormalised.  About 48 bits, in FP32 arithmetic.
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    const float s = a.x + b.x, bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (b.x - bb) + (a.y + b.y);
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

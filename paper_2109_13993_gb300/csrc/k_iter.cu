@@ -223,14 +223,6 @@ struct FF {
     __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };
 
-// Sum of two float-float values (hi, lo): TwoSum of the high parts, the low parts added to
-// its error, renormalised.  About 48 bits, in FP32 arithmetic.
-__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
-    const float s = a.x + b.x, bb = s - a.x;
-    const float e = (a.x - (s - bb)) + (b.x - bb) + (a.y + b.y);
-    const float hi = s + e;
-    return make_float2(hi, e - (hi - s));
-}
 
 // 16 consecutive values (16-byte aligned) through L2.
 __device__ __forceinline__ void load16_cg(float* v, const float* src) {

@@ -13,6 +13,99 @@ constexpr int kRowThreads = 256;
 // One CTA per row: mean, standard deviation with divisor n-1 (both FP64), the
 // padded normalised row (zeros beyond n) and H(x) - H(nu).  Sample t of the row is
 // xr[t], or xr[idx[t]] when idx is given (a bootstrap resample of the columns).
+// The FP32 working copy (mixed path) in float-float arithmetic: FP64 operations are slow on
+// this part, and float-float sums keep about 48 bits.  The sum of the samples and the sum of
+// the squared deviations are float-float (a sample of an FP64 input enters as its
+// float-float split; a deviation v - mu is formed exactly by TwoSum and its square by
+// TwoProd); mean, variance and 1/sd are formed once per row in FP64.  The normalised sample
+// is the float-float deviation times 1/sd (float-float), rounded once to FP32.
+__device__ __forceinline__ float2 ff_of(float v) { return make_float2(v, 0.f); }
+__device__ __forceinline__ float2 ff_of(double v) {
+    const float hi = float(v);
+    return make_float2(hi, float(v - double(hi)));
+}
+// a - (mh + ml) as float-float
+__device__ __forceinline__ float2 ff_dev(float2 a, float mh, float ml) {
+    return ff_add(a, make_float2(-mh, -ml));
+}
+// Fixed-order float-float block sum; the result to every thread.
+__device__ __forceinline__ float2 block_ff_sum(float2 v, float2* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = ff_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    float2 s = red[0];
+    for (int w = 1; w < kRowThreads / 32; ++w) s = ff_add(s, red[w]);
+    return s;
+}
+
+template <class Tin>
+__device__ void standardize_row_ff(const Fit& f, const Tin* __restrict__ xr, const int* __restrict__ idx, int row,
+                                   float2* red, double* bc) {
+    const int n = f.n, ld = f.ld, tid = threadIdx.x;
+    auto at = [&](int t) { return idx ? xr[idx[t]] : xr[t]; };
+    float2 s = make_float2(0.f, 0.f);
+    bool finite = true;
+    for (int t = tid; t < n; t += kRowThreads) {
+        const Tin v = at(t);
+        finite &= isfinite(v);
+        s = ff_add(s, ff_of(v));
+    }
+    if (__syncthreads_or(!finite)) {
+        if (tid == 0) set_status(f.ctl, LINGAM_EDEGENERATE);
+        return;
+    }
+    s = block_ff_sum(s, red);
+    if (tid == 0) bc[0] = (double(s.x) + double(s.y)) / double(n);
+    __syncthreads();
+    const double mu = bc[0];
+    const float mh = float(mu), ml = float(mu - double(mh));
+    float2 q = make_float2(0.f, 0.f);
+    for (int t = tid; t < n; t += kRowThreads) {
+        const float2 d = ff_dev(ff_of(at(t)), mh, ml);
+        const float sq = d.x * d.x;
+        q = ff_add(q, make_float2(sq, fmaf(d.x, d.x, -sq) + 2.f * d.x * d.y));
+    }
+    q = block_ff_sum(q, red);
+    if (tid == 0) {
+        const double var = (double(q.x) + double(q.y)) / double(n - 1);
+        bc[1] = var;
+        bc[2] = 1.0 / sqrt(var);
+    }
+    __syncthreads();
+    const double var = bc[1];
+    if (!(var > 0.0) || !isfinite(var)) {
+        if (tid == 0) set_status(f.ctl, LINGAM_EDEGENERATE);
+        return;
+    }
+    // 1/sd as float-float, so that a row is not scaled by the FP32 rounding of 1/sd
+    const float ih = float(bc[2]), il = float(bc[2] - double(ih));
+    float* out = static_cast<float*>(f.xt) + size_t(row) * ld;
+    float lcc = 0.f, g = 0.f;
+    for (int t = tid; t < ld; t += kRowThreads) {
+        float u = 0.f;
+        if (t < n) {
+            const float2 d = ff_dev(ff_of(at(t)), mh, ml);
+            u = fmaf(d.x, ih, fmaf(d.x, il, d.y * ih));
+            mom_add(u, lcc, g);
+        }
+        out[t] = u;
+    }
+    const float2 L = block_ff_sum(make_float2(lcc, 0.f), red);
+    const float2 G = block_ff_sum(make_float2(g, 0.f), red);
+    if (tid == 0) {
+        const double Ld = double(L.x) + double(L.y), Gd = double(G.x) + double(G.y);
+        f.mu[row] = mu;
+        f.sd[row] = sqrt(var);
+        f.hx[row] = hterm_inv(Ld, Gd, f.inv_n);
+        f.vstat[row] = var_stats_inv(Ld, Gd, n, ld, f.inv_n);
+        f.flags[row] = kAlive;
+    }
+}
+
 template <class Tin, class T>
 __device__ void standardize_row(const Fit& f, const Tin* __restrict__ xr, const int* __restrict__ idx, int row,
                                 double* red) {
@@ -61,10 +154,23 @@ __device__ void standardize_row(const Fit& f, const Tin* __restrict__ xr, const 
     }
 }
 
+// One row of the working copy: float-float arithmetic for an FP32 copy, FP64 for an FP64 one.
+template <class Tin, class T>
+__device__ __forceinline__ void normalise_row(const Fit& f, const Tin* __restrict__ xr, const int* __restrict__ idx,
+                                              int row) {
+    if constexpr (std::is_same<T, float>::value) {
+        __shared__ float2 red2[kRowThreads / 32];
+        __shared__ double bc[3];
+        standardize_row_ff<Tin>(f, xr, idx, row, red2, bc);
+    } else {
+        __shared__ double red[kRowThreads / 32];
+        standardize_row<Tin, T>(f, xr, idx, row, red);
+    }
+}
+
 template <class Tin, class T>
 __global__ void __launch_bounds__(kRowThreads) k_standardize(Fit f, const Tin* __restrict__ x) {
-    __shared__ double red[kRowThreads / 32];
-    standardize_row<Tin, T>(f, x + size_t(blockIdx.x) * f.n, nullptr, blockIdx.x, red);
+    normalise_row<Tin, T>(f, x + size_t(blockIdx.x) * f.n, nullptr, blockIdx.x);
 }
 
 // All rows of many problems: CTA g takes row g - rowoff[d] of the problem d with
@@ -73,7 +179,6 @@ template <class Tin, class T>
 __global__ void __launch_bounds__(kRowThreads) k_standardize_batch(const Fit* __restrict__ fits,
                                                                  const SrcDesc* __restrict__ src,
                                                                  const int* __restrict__ rowoff, int count) {
-    __shared__ double red[kRowThreads / 32];
     const int g = blockIdx.x;
     int lo = 0, hi = count - 1;
     while (lo < hi) {
@@ -85,7 +190,7 @@ __global__ void __launch_bounds__(kRowThreads) k_standardize_batch(const Fit* __
     if (((volatile Ctl*)f.ctl)->status != 0) return;
     const int row = g - rowoff[lo];
     const SrcDesc sd = src[lo];
-    standardize_row<Tin, T>(f, static_cast<const Tin*>(sd.x) + size_t(row) * sd.ld, sd.idx, row, red);
+    normalise_row<Tin, T>(f, static_cast<const Tin*>(sd.x) + size_t(row) * sd.ld, sd.idx, row);
 }
 
 // Per-problem start of a batch: orders unset, tile counters and report arrays zero.
