@@ -42,36 +42,53 @@ __device__ __forceinline__ float2 block_ff_sum(float2 v, float2* red) {
     return s;
 }
 
+// Returns false (before any write) when the row's largest magnitude lies outside
+// [2^-60, 2^60]: there the float-float sums could overflow or lose their low parts, and the
+// caller takes the FP64 routine.
 template <class Tin>
-__device__ void standardize_row_ff(const Fit& f, const Tin* __restrict__ xr, const int* __restrict__ idx, int row,
+__device__ bool standardize_row_ff(const Fit& f, const Tin* __restrict__ xr, const int* __restrict__ idx, int row,
                                    float2* red, double* bc) {
     const int n = f.n, ld = f.ld, tid = threadIdx.x;
     auto at = [&](int t) { return idx ? xr[idx[t]] : xr[t]; };
     float2 s = make_float2(0.f, 0.f);
+    float amax = 0.f;
     bool finite = true;
     for (int t = tid; t < n; t += kRowThreads) {
         const Tin v = at(t);
         finite &= isfinite(v);
         s = ff_add(s, ff_of(v));
+        amax = fmaxf(amax, fabsf(float(v)));
     }
     if (__syncthreads_or(!finite)) {
         if (tid == 0) set_status(f.ctl, LINGAM_EDEGENERATE);
-        return;
+        return true;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((tid & 31) == 0) red[tid >> 5].x = amax;
+    __syncthreads();
+    amax = red[0].x;
+    for (int w = 1; w < kRowThreads / 32; ++w) amax = fmaxf(amax, red[w].x);
+    if (!(amax >= 0x1p-60f && amax <= 0x1p60f)) return false;   // the same for every thread
     s = block_ff_sum(s, red);
     if (tid == 0) bc[0] = (double(s.x) + double(s.y)) / double(n);
     __syncthreads();
     const double mu = bc[0];
     const float mh = float(mu), ml = float(mu - double(mh));
+    // the deviations scaled by 2^-e (exactly), |v| < 2^(e+1), so that their squares stay in range
+    const int e = ilogbf(amax);
+    const float sc = ldexpf(1.f, -e);
     float2 q = make_float2(0.f, 0.f);
     for (int t = tid; t < n; t += kRowThreads) {
-        const float2 d = ff_dev(ff_of(at(t)), mh, ml);
+        float2 d = ff_dev(ff_of(at(t)), mh, ml);
+        d.x *= sc;
+        d.y *= sc;
         const float sq = d.x * d.x;
         q = ff_add(q, make_float2(sq, fmaf(d.x, d.x, -sq) + 2.f * d.x * d.y));
     }
     q = block_ff_sum(q, red);
     if (tid == 0) {
-        const double var = (double(q.x) + double(q.y)) / double(n - 1);
+        const double var = ldexp(double(q.x) + double(q.y), 2 * e) / double(n - 1);
         bc[1] = var;
         bc[2] = 1.0 / sqrt(var);
     }
@@ -79,7 +96,7 @@ __device__ void standardize_row_ff(const Fit& f, const Tin* __restrict__ xr, con
     const double var = bc[1];
     if (!(var > 0.0) || !isfinite(var)) {
         if (tid == 0) set_status(f.ctl, LINGAM_EDEGENERATE);
-        return;
+        return true;
     }
     // 1/sd as float-float, so that a row is not scaled by the FP32 rounding of 1/sd
     const float ih = float(bc[2]), il = float(bc[2] - double(ih));
@@ -104,6 +121,7 @@ __device__ void standardize_row_ff(const Fit& f, const Tin* __restrict__ xr, con
         f.vstat[row] = var_stats_inv(Ld, Gd, n, ld, f.inv_n);
         f.flags[row] = kAlive;
     }
+    return true;
 }
 
 template <class Tin, class T>
@@ -154,18 +172,19 @@ __device__ void standardize_row(const Fit& f, const Tin* __restrict__ xr, const 
     }
 }
 
-// One row of the working copy: float-float arithmetic for an FP32 copy, FP64 for an FP64 one.
+// One row of the working copy: float-float arithmetic for an FP32 copy (FP64 for a row whose
+// magnitudes leave [2^-60, 2^60]), FP64 for an FP64 one.
 template <class Tin, class T>
 __device__ __forceinline__ void normalise_row(const Fit& f, const Tin* __restrict__ xr, const int* __restrict__ idx,
                                               int row) {
+    __shared__ double red[kRowThreads / 32];
     if constexpr (std::is_same<T, float>::value) {
         __shared__ float2 red2[kRowThreads / 32];
         __shared__ double bc[3];
-        standardize_row_ff<Tin>(f, xr, idx, row, red2, bc);
-    } else {
-        __shared__ double red[kRowThreads / 32];
-        standardize_row<Tin, T>(f, xr, idx, row, red);
+        if (standardize_row_ff<Tin>(f, xr, idx, row, red2, bc)) return;
+        __syncthreads();   // red2 is not reused, but keep the fallback's start ordered
     }
+    standardize_row<Tin, T>(f, xr, idx, row, red);
 }
 
 template <class Tin, class T>

@@ -124,3 +124,25 @@ def test_long_rows_n_1e6_first_iterations():
     assert np.all(np.isnan(res.scores[1][[r0]]))
     print(f"p=50, n=1e6: max |dS| iteration 0 {e0:.2e}, iteration 1 {e1:.2e}")
     assert e0 <= TOL and e1 <= TOL
+
+
+def test_extreme_row_scales():
+    """Rows scaled over 10^-30 ... 3 x 10^30 (all FP32-representable): NormalizeData of the
+    FP32 copy runs in float-float arithmetic for rows whose magnitudes lie in [2^-60, 2^60]
+    (its squared deviations scaled by an exact power of two) and in FP64 outside, so that
+    neither overflows nor underflows.  Forced along the oracle's order, every score is within
+    the tolerance and B, brought back to unit scales, within 1e-4."""
+    d = synth.lingam_dataset(8, 2000, 0.4, seed=11)
+    scales = np.array([1e25, 1e-25, 1e15, 1.0, 1e-15, 3e30, 1e-30, 7.0])
+    X32 = (d.X * scales[:, None]).astype(np.float32)
+    assert np.all(np.isfinite(X32)) and np.all(np.abs(X32[X32 != 0]) > 1e-37)
+    o_order, o_B, o_S = oracle.fit(X32.astype(np.float64))
+    res = lingam.fit(_dev(X32), precision="mixed", prune=False, forced_order=o_order, want_scores=True)
+    m = ~np.isnan(res.scores)
+    assert np.array_equal(m, ~np.isnan(o_S))
+    err = float(np.abs(res.scores[m] - o_S[m]).max())
+    unit = scales[None, :] / scales[:, None]   # B_ij s_j / s_i: the coefficients at unit scales
+    eB = float(np.abs(res.B * unit - o_B * unit).max()) / max(1.0, float(np.abs(o_B * unit).max()))
+    print(f"row scales 1e-30 .. 3e30: max |dS| {err:.2e}, B (unit scales) {eB:.2e}")
+    assert err <= TOL
+    assert eB <= 1e-4
