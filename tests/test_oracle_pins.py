@@ -397,7 +397,7 @@ _BRUTE_CASES = [(3, 2000, 11), (4, 3000, 12), (5, 4000, 13), (6, 5000, 14), (6, 
 
 @pytest.mark.parametrize("p,n,seed", _BRUTE_CASES)
 def test_every_score_of_every_iteration_by_brute_force(oracle_mod, p, n, seed):
-    """North-star pin: on seeded p <= 6 DAGs every S_i of every iteration, recomputed by the
+    """Brute-force pin: on seeded p <= 6 DAGs every S_i of every iteration, recomputed by the
     naive formula above, equals the oracle's within 1e-12 (absolute), and so does the order."""
     d = synth.lingam_dataset(p, n, 0.6, seed=seed)
     order_b, S_b = _naive_directlingam(d.X)
