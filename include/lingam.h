@@ -35,9 +35,10 @@
  *   - Data pointers may point to host or device memory; the library tells
  *     them apart with cudaPointerGetAttributes.  Host buffers are copied
  *     inside the call.  All device work is ordered on opts->stream (a batch
- *     forks its per-problem covariances onto the library's streams and joins
- *     them back into it) and the call returns after that stream has drained
- *     (it is synchronous).
+ *     forks the covariances of its problems above 128 variables or 2048
+ *     samples onto the library's streams and joins them back into it; the
+ *     smaller problems' covariances are one launch on opts->stream) and the
+ *     call returns after that stream has drained (it is synchronous).
  *   - The device is the CUDA device current on the calling thread.
  *   - Environment variables, read by the library: LINGAM_LOG=1 prints one
  *     line per call on stderr (entry point, sizes, status); LINGAM_FAULT=<step>
