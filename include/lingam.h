@@ -227,7 +227,9 @@ int lingam_covariance(const void* X, long long p, long long n, double* Sigma, vo
  *                       largest problem has maxp variables and maxn samples, when
  *                       opts->tile_i and opts->tile_j are 0.  Batches have a table of their
  *                       own (bucket of the largest p and n); a bucket never measured uses
- *                       32 x 32, which pads least once problems are down to r < 32.
+ *                       the pair mode, 1 x 1, when maxp <= 128 (it was the fastest shape on
+ *                       every measured batch of small problems), else 32 x 32.  With
+ *                       opts->reuse = 0 the pair mode runs as 64 x 16.
  * lingam_autotune_batch -- measures lingam_fit_batch on the caller's count datasets (as
  *                       lingam_fit_batch with opts on the mixed path, B not fitted) with
  *                       each shape: a warm-up call, the call that captures the graph, and

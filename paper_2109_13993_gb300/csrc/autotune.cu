@@ -52,7 +52,10 @@ static std::map<std::pair<int, int>, TileShape> g_tune_batch;
 TileShape autotune_batch_shape(long long maxp, long long maxn) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_batch.find(bucket(maxp, maxn));
-    return it != g_tune_batch.end() ? it->second : TileShape{32, 32};
+    if (it != g_tune_batch.end()) return it->second;
+    // never measured: the pair-per-warp mode up to 128 variables (it wins over every tile
+    // shape on the measured batches of small problems), else 32 x 32
+    return maxp <= 128 ? TileShape{1, 1} : TileShape{32, 32};
 }
 
 void autotune_batch_record(long long maxp, long long maxn, TileShape shape) {

@@ -158,9 +158,11 @@ static bool valid_opts(const lingam_opts& o) {
 // autotuner's table for the largest p and n; the FP64 path has 32 x 32 tiles only.
 static TileShape batch_tile_shape(const lingam_opts& o, long long maxp, long long maxn) {
     if (o.precision != LINGAM_MIXED) return TileShape{32, 32};
-    if (o.tile_i == 1 && o.tile_j == 1 && !o.reuse) return TileShape{64, 16};   // pair mode evaluates unordered pairs
-    if (o.tile_i != 0 || o.tile_j != 0) return TileShape{o.tile_i ? o.tile_i : 64, o.tile_j ? o.tile_j : 32};
-    return autotune_batch_shape(maxp, maxn);
+    const TileShape t = (o.tile_i != 0 || o.tile_j != 0)
+                            ? TileShape{o.tile_i ? o.tile_i : 64, o.tile_j ? o.tile_j : 32}
+                            : autotune_batch_shape(maxp, maxn);
+    if (t.rows == 1 && t.cols == 1 && !o.reuse) return TileShape{64, 16};   // pair mode evaluates unordered pairs
+    return t;
 }
 
 // Single fits run 64 x 32, 32 x 32 or 64 x 16 tiles (32 x 16 tiles and the pair-per-warp

@@ -70,8 +70,10 @@ def test_tile_rows_default_rule(lib):
     assert lingam.tile_rows(1000, 10000) == 64
     assert lingam.tile_rows(0, 100) == 0
     assert lingam.tile_shape(1000, 10000) == (64, 32)
-    # batches: a table of their own, default 32 x 32
-    assert lingam.batch_tile_shape(50, 2000) == (32, 32)
+    # batches: a table of their own, untuned default the pair mode up to 128 variables
+    assert lingam.batch_tile_shape(50, 2000) == (1, 1)
+    assert lingam.batch_tile_shape(128, 8000) == (1, 1)
+    assert lingam.batch_tile_shape(129, 2000) == (32, 32)
     assert lingam.batch_tile_shape(1000, 10000) == (32, 32)
     assert lib.lingam_batch_tile_rows(0, 100) == 0
     o, _ = lingam.make_opts()
