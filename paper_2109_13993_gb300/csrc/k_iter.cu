@@ -2478,11 +2478,9 @@ __global__ void __launch_bounds__(kPairThr, 2) k_batch_pairs(const Fit* __restri
     unsigned char* smem_raw = smem_dyn;
     __shared__ IterShared sh;
     __shared__ BatchShared bs;
-    constexpr int NW = kPairThr / 32;
     volatile Ctl* vb = bctl;
     if (vb->status != 0) return;
     const unsigned long long tmo = vb->timeout_ns;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int it = 0; it < maxp; ++it) {
         batch_active(fits, count, it, 0, bs);
         for (int d = blockIdx.x; d < count; d += gridDim.x)
